@@ -1,0 +1,167 @@
+/*
+ * aspgpu -- conflict-driven answer-set solving on one GB300 (sm_103a).
+ *
+ * C ABI of libaspgpu.so.  Every entry point takes plain host or device
+ * pointers and sizes; no C++ or framework types cross this boundary.
+ *
+ * Method: Dovier, Formisano, Vella, "GPU-based parallelism for ASP-solving"
+ * (arXiv 1909.01786).  A ground normal program is turned into completion
+ * nogoods (Section 2), stored as a nogood store in device memory (Section 4),
+ * and solved by conflict-driven nogood learning with ASP-computation
+ * decisions (Section 2; Algorithm 1): propagation and checking of all
+ * nogoods to a fixpoint (Section 4.1), conflict analysis from decision-level
+ * dependency bitmaps (Section 4.2, Algorithm 4), backjumping, decisions, and
+ * completion of the assignment.  Every step runs in this library's CUDA
+ * kernels; the host only builds the nogood store and reads results.
+ *
+ * Conventions
+ *  - Atoms are 0-based.  Rule r is  head[r] <- pos[pos_off[r]..pos_off[r+1]),
+ *    not neg[neg_off[r]..neg_off[r+1]);  head[r] = -1 marks an integrity
+ *    constraint (Section 1).  Repeated atoms in one body count once.
+ *  - Solver variables: atoms 0..n_atoms-1, then for the j-th rule that has a
+ *    head (rules ordered by head atom, ties in input order)
+ *    b_j = n_atoms + 3j, t_j = n_atoms + 3j + 1, n_j = n_atoms + 3j + 2 (the
+ *    auxiliary atoms b_r, t_r, n_r of Section 2).
+ *  - Models are bitsets: row i of a model buffer holds ceil(n_atoms/64)
+ *    uint64 words; bit (a mod 64) of word (a div 64) is atom a.
+ *  - Return codes: ASP_OK or a negative ASP_E_*; asp_last_error() gives a
+ *    message (thread-local).  Status values follow the SAT convention.
+ *  - A program object is used by one host thread at a time; calls on
+ *    different program objects may run concurrently on different streams.
+ */
+#ifndef ASPGPU_H
+#define ASPGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASP_OK 0
+#define ASP_E_ARG (-1)       /* bad argument (null pointer, negative size, bad offsets) */
+#define ASP_E_RANGE (-2)     /* atom id out of range, or too many variables */
+#define ASP_E_OOM (-3)       /* device allocation failed */
+#define ASP_E_CUDA (-4)      /* CUDA runtime error */
+#define ASP_E_CAPACITY (-5)  /* caller's model buffer full; the models found so far are valid */
+#define ASP_E_DEVICE (-6)    /* device-side error: learned-store overflow or barrier timeout */
+#define ASP_E_NODEVICE (-7)  /* no CUDA device / compiled kernels unavailable */
+
+#define ASP_STATUS_UNKNOWN 0 /* budget exhausted before the answer was known */
+#define ASP_STATUS_SAT 10    /* at least one answer set found */
+#define ASP_STATUS_UNSAT 20  /* no (further) answer set exists */
+
+#define ASP_HEUR_OCCURRENCE 0 /* static: occurrence count of the head (Section 4) */
+#define ASP_HEUR_ACTIVITY 1   /* occurrence count plus activity bumped by conflicts */
+
+typedef struct asp_prog asp_prog; /* opaque, owned by the library */
+
+typedef struct {
+    int32_t heuristic;        /* ASP_HEUR_* */
+    int32_t deps_levels;      /* decision levels tracked exactly by the dependency
+                                 bitmaps (Section 4.2); rounded up to a multiple of 64;
+                                 deeper levels share one overflow bit. 0 = 4096 */
+    int64_t conflict_budget;  /* stop with UNKNOWN after this many conflicts; 0 = none */
+    int64_t time_budget_ms;   /* stop with UNKNOWN after this device time; 0 = none */
+    int64_t learned_capacity; /* literals reserved for learned nogoods; 0 = automatic */
+    int32_t grid_ctas;        /* CTAs of the persistent solver grid; 0 = one per SM */
+    int32_t block_threads;    /* threads per CTA (multiple of 32, <= 768); 0 = 768 */
+    void *cuda_stream;        /* cudaStream_t for all work of this program; NULL = default */
+    /* device memory hooks; both NULL = cudaMalloc/cudaFree */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, size_t bytes, void *ctx);
+    void *alloc_ctx;
+} asp_options;
+
+typedef struct {
+    int64_t n_vars, n_atoms, n_rules_with_head;
+    int64_t n_nogoods, n_literals;       /* static completion + constraint nogoods */
+    int64_t n_unit_nogoods, n_long_nogoods;
+    int64_t store_bytes;                 /* device bytes of the static nogood store */
+    int64_t rounds;                      /* propagate-and-check sweeps (Section 4.1) */
+    int64_t literal_checks;              /* literals read and classified by the sweeps */
+    int64_t propagations, conflicts, decisions, completions;
+    int64_t learned, learned_literals, loop_nogoods, models;
+    int64_t max_level;
+    int64_t ns_total, ns_sweep, ns_analysis, ns_decision, ns_stability; /* device time */
+} asp_stats_t;
+
+/* Default options (all zero except as documented above). */
+void asp_default_options(asp_options *opt);
+
+/* Build the completion nogoods of a ground normal program (Section 2) and
+ * upload them.  Input arrays belong to the caller and are only read during
+ * the call.  opt may be NULL.  On success *out owns device memory until
+ * asp_free.  Errors: ASP_E_ARG, ASP_E_RANGE, ASP_E_OOM, ASP_E_CUDA,
+ * ASP_E_NODEVICE. */
+int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
+                    const int64_t *pos_off, const int32_t *pos,
+                    const int64_t *neg_off, const int32_t *neg,
+                    const asp_options *opt, asp_prog **out);
+
+/* Search for answer sets (Algorithm 1 on the device): up to max_models of
+ * them (0 = all).  models: host buffer of models_cap rows (see Conventions).
+ * Blocks until done.  status: ASP_STATUS_*; n_models: answer sets found.
+ * Returns ASP_E_CAPACITY if more models were found than models_cap rows
+ * (the first models_cap rows are written; *n_models is the count found). */
+int asp_solve(asp_prog *p, int64_t max_models, uint64_t *models, int64_t models_cap,
+              int64_t *n_models, int32_t *status);
+
+/* Device-resident form of asp_solve: enqueues the whole search on the
+ * program's stream and returns without synchronising.  d_models is a device
+ * buffer of models_cap rows; d_result is a device int64[4] receiving
+ * {status, n_models, error_code, 0}.  Sizes are as for asp_solve. */
+int asp_solve_async(asp_prog *p, int64_t max_models, uint64_t *d_models, int64_t models_cap,
+                    int64_t *d_result);
+
+/* Solve n independent programs in one persistent launch, one CTA per program
+ * at a time, taking programs from a device work queue largest first.
+ * progs[i] must have been loaded with the same stream.  statuses[i],
+ * n_models[i] are host outputs; models[i] (host, models_cap[i] rows) may be
+ * NULL when models_cap[i] is 0. */
+int asp_solve_batch(int32_t n, asp_prog *const *progs, int64_t max_models_each,
+                    int32_t *statuses, int64_t *n_models, uint64_t *const *models,
+                    const int64_t *models_cap);
+
+/* Counters of the last solve on this program (device time in ns). */
+int asp_stats(const asp_prog *p, asp_stats_t *out);
+
+/* Release all device memory of the program. */
+void asp_free(asp_prog *p);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *asp_last_error(void);
+
+/* ---- test and measurement entry points ---------------------------------
+ * Unit propagation to fixpoint alone (Section 4.1, propagate-and-check):
+ * partial[v] in {1 true, -1 false, 0 unassigned} over all solver variables
+ * (host, n_vars entries), taken as root-level input; the static nogoods are
+ * then swept until no nogood is unit.  closure (host, n_vars) receives the
+ * result; *conflict = 1 if some nogood became violated (closure is then the
+ * state at that point).  The input must not itself assign a variable twice;
+ * it may violate nogoods. */
+int asp_debug_propagate(asp_prog *p, const int8_t *partial, int8_t *closure, int32_t *conflict);
+
+/* One propagate-and-check sweep over the whole static store against the
+ * current device assignment, without committing anything (used to time the
+ * sweep kernel in isolation).  Enqueued on the program's stream. */
+int asp_sweep_once(asp_prog *p);
+
+/* Copy of the state after the last solve or debug call, for consistency
+ * checks: trail (n_trail variables in assignment order), per variable
+ * level (int32, 0 = unassigned), reason (uint32 nogood id, 0xFFFFFFFF =
+ * decision, 0xFFFFFFFE = completion step, 0xFFFFFFFD = input) and the first
+ * deps_words uint64 words of each variable's dependency bitmap.  Host
+ * buffers; any may be NULL.  *n_trail receives the trail length. */
+int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *level,
+                    uint32_t *reason, uint64_t *deps, int32_t deps_words);
+
+/* Literals of nogood `id` (a reason or learned id) as (var << 1 | sign),
+ * sign 1 = F; returns the length, writes at most cap literals. */
+int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASPGPU_H */

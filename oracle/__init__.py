@@ -148,10 +148,10 @@ def cdnl(prog, max_models: int = 0, conflict_budget: int = 0, time_budget_s: flo
     cap = max(cap, 1)
     buf = np.zeros((cap, width), dtype=np.uint8)
     nm = C.c_int64()
-    st = np.zeros(4, dtype=np.int64)
+    st = np.zeros(5, dtype=np.int64)
     status = _load().oracle_cdnl(b.ref, int(max_models), int(conflict_budget), float(time_budget_s),
                                  _ptr(buf), cap, C.byref(nm), _ptr(st))
     n = min(nm.value, cap)
     stats = dict(decisions=int(st[0]), conflicts=int(st[1]), propagations=int(st[2]),
-                 learned=int(st[3]), n_models=int(nm.value))
+                 learned=int(st[3]), literal_checks=int(st[4]), n_models=int(nm.value))
     return status, buf[:n, :prog.n_atoms].copy(), stats

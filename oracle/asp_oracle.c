@@ -353,6 +353,7 @@ typedef struct {
     int32_t *tmp;
     int64_t tmp_cap;
     int64_t conflicts, decisions, propagations;
+    int64_t literal_checks;    /* literals read and classified (instrumentation) */
 } cdnl;
 
 static void occ_push(cdnl *S, int32_t v, int64_t g)
@@ -395,11 +396,12 @@ static void backjump(cdnl *S, int32_t level)
 
 /* 0 = satisfied or open, 1 = unit (out = the single literal not in A),
  * 2 = violated */
-static int classify(const cdnl *S, int64_t g, int32_t *out)
+static int classify(cdnl *S, int64_t g, int32_t *out)
 {
     int64_t n_out = 0;
     for (int64_t k = S->db.off[g]; k < S->db.off[g + 1]; k++) {
         int32_t l = S->db.lit[k];
+        S->literal_checks++;
         if (lit_opposed(S->val, l)) return 0;
         if (!lit_holds(S->val, l)) { n_out++; *out = l; if (n_out > 1) return 0; }
     }
@@ -646,6 +648,7 @@ done_budget:
         stats[1] = S.conflicts;
         stats[2] = S.propagations;
         stats[3] = S.db.n - S.n_static;
+        stats[4] = S.literal_checks;
     }
     for (int32_t v = 0; v < S.nv; v++) free(S.occ[v]);
     free(S.occ); free(S.occ_n); free(S.occ_cap);

@@ -1,0 +1,6 @@
+"""GB300-native conflict-driven answer-set solving (arXiv 1909.01786).
+
+The solver is the CUDA library ``libaspgpu.so`` behind the C ABI in
+``include/aspgpu.h``; ``aspgpu`` is its Python binding.
+"""
+from .aspgpu import AspError, Program, SAT, UNSAT, UNKNOWN, lib, solve_batch, words_to_models  # noqa: F401

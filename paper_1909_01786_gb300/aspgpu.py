@@ -1,0 +1,250 @@
+"""ctypes binding of libaspgpu (include/aspgpu.h): argument marshalling only.
+
+Every step of the search runs in the library's CUDA kernels.  There is no
+fallback: if the compiled library or a CUDA device is missing, calls raise.
+PyTorch, when present, provides device memory (its caching allocator) and
+streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ASP_OK, ASP_E_CAPACITY = 0, -5
+SAT, UNSAT, UNKNOWN = 10, 20, 0
+R_DECISION, R_COMPLETE, R_INPUT = 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD
+
+_lib = None
+_lock = threading.Lock()
+
+
+class AspError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"aspgpu error {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("heuristic", C.c_int32), ("deps_levels", C.c_int32),
+                ("conflict_budget", C.c_int64), ("time_budget_ms", C.c_int64),
+                ("learned_capacity", C.c_int64), ("grid_ctas", C.c_int32),
+                ("block_threads", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "n_vars", "n_atoms", "n_rules_with_head", "n_nogoods", "n_literals",
+        "n_unit_nogoods", "n_long_nogoods", "store_bytes", "rounds", "literal_checks",
+        "propagations", "conflicts", "decisions", "completions", "learned",
+        "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
+        "ns_sweep", "ns_analysis", "ns_decision", "ns_stability")]
+
+
+EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
+           "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep_once",
+           "asp_debug_state", "asp_debug_nogood"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libaspgpu.so (building it in-tree if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(path):
+            raise AspError(-7, f"{path} not built")
+        L = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.asp_default_options.argtypes = [vp]
+        L.asp_default_options.restype = None
+        L.asp_load_ground.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.asp_load_ground.restype = C.c_int
+        L.asp_solve.argtypes = [vp, i64, vp, i64, vp, vp]
+        L.asp_solve.restype = C.c_int
+        L.asp_solve_async.argtypes = [vp, i64, vp, i64, vp]
+        L.asp_solve_async.restype = C.c_int
+        L.asp_solve_batch.argtypes = [i32, vp, i64, vp, vp, vp, vp]
+        L.asp_solve_batch.restype = C.c_int
+        L.asp_stats.argtypes = [vp, vp]
+        L.asp_stats.restype = C.c_int
+        L.asp_free.argtypes = [vp]
+        L.asp_free.restype = None
+        L.asp_last_error.argtypes = []
+        L.asp_last_error.restype = C.c_char_p
+        L.asp_debug_propagate.argtypes = [vp, vp, vp, vp]
+        L.asp_debug_propagate.restype = C.c_int
+        L.asp_sweep_once.argtypes = [vp]
+        L.asp_sweep_once.restype = C.c_int
+        L.asp_debug_state.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+        L.asp_debug_state.restype = C.c_int
+        L.asp_debug_nogood.argtypes = [vp, C.c_uint32, vp, i64]
+        L.asp_debug_nogood.restype = i64
+        _lib = L
+        return L
+
+
+def _check(rc, ok=(ASP_OK,)):
+    if rc not in ok:
+        raise AspError(rc, lib().asp_last_error().decode())
+    return rc
+
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator on the given stream."""
+
+    def __init__(self, torch, device, stream):
+        self.torch, self.device, self.stream = torch, device, stream
+
+        def alloc(n, ctx):
+            return self.torch.cuda.caching_allocator_alloc(int(n), device=self.device, stream=self.stream)
+
+        def free(p, n, ctx):
+            self.torch.cuda.caching_allocator_delete(p)
+
+        self.c_alloc, self.c_free = _ALLOC(alloc), _FREE(free)
+
+
+def words_to_models(words: np.ndarray, n_atoms: int) -> np.ndarray:
+    """uint64 model rows -> uint8 [rows, n_atoms]."""
+    if words.shape[0] == 0:
+        return np.zeros((0, n_atoms), dtype=np.uint8)
+    b = np.unpackbits(words.astype("<u8").view(np.uint8).reshape(words.shape[0], -1), axis=1, bitorder="little")
+    return b[:, :n_atoms].copy()
+
+
+class Program:
+    """A ground program loaded on the GPU (asp_load_ground)."""
+
+    def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
+                 learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True):
+        L = lib()
+        self.n_atoms = int(prog.n_atoms)
+        self._keep = []
+        opt = Options()
+        L.asp_default_options(C.byref(opt))
+        opt.heuristic, opt.deps_levels = heuristic, deps_levels
+        opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
+        opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads
+        self._alloc = None
+        if torch_memory:
+            try:
+                import torch
+            except ImportError:
+                torch = None
+            if torch is not None and torch.cuda.is_available():
+                dev = torch.cuda.current_device()
+                s = stream if stream is not None else torch.cuda.current_stream(dev)
+                self._alloc = _TorchAllocator(torch, dev, s)
+                opt.cuda_stream = s.cuda_stream
+                opt.dev_alloc = C.cast(self._alloc.c_alloc, C.c_void_p).value
+                opt.dev_free = C.cast(self._alloc.c_free, C.c_void_p).value
+                self.stream = s
+        arrs = [np.ascontiguousarray(prog.head, np.int32), np.ascontiguousarray(prog.pos_off, np.int64),
+                np.ascontiguousarray(prog.pos, np.int32), np.ascontiguousarray(prog.neg_off, np.int64),
+                np.ascontiguousarray(prog.neg, np.int32)]
+        h = C.c_void_p()
+        _check(L.asp_load_ground(self.n_atoms, int(prog.head.shape[0]),
+                                 *[a.ctypes.data if a.size else None for a in arrs],
+                                 C.byref(opt), C.byref(h)))
+        self.handle = h
+        self.words = (self.n_atoms + 63) // 64
+        st = self.stats()
+        self.n_vars = st["n_vars"]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().asp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, max_models: int = 0, cap: int | None = None, raw: bool = False):
+        """Returns (status, models uint8 [n, n_atoms], n_found)."""
+        if cap is None:
+            cap = max_models if max_models > 0 else 4096
+        buf = np.zeros((max(cap, 1), max(self.words, 1)), dtype=np.uint64)
+        n = C.c_int64()
+        st = C.c_int32()
+        rc = lib().asp_solve(self.handle, int(max_models), buf.ctypes.data, int(cap), C.byref(n), C.byref(st))
+        _check(rc, ok=(ASP_OK, ASP_E_CAPACITY))
+        rows = buf[:min(n.value, cap)]
+        return st.value, (rows if raw else words_to_models(rows, self.n_atoms)), n.value
+
+    def solve_async(self, max_models: int, d_models_ptr: int, cap: int, d_result_ptr: int):
+        _check(lib().asp_solve_async(self.handle, int(max_models), d_models_ptr or None, int(cap), d_result_ptr))
+
+    def propagate(self, partial: np.ndarray):
+        """Unit propagation of a partial assignment over all variables."""
+        p = np.ascontiguousarray(partial, dtype=np.int8)
+        assert p.shape[0] == self.n_vars
+        out = np.zeros(self.n_vars, dtype=np.int8)
+        conf = C.c_int32()
+        _check(lib().asp_debug_propagate(self.handle, p.ctypes.data, out.ctypes.data, C.byref(conf)))
+        return bool(conf.value), out
+
+    def sweep_once(self):
+        _check(lib().asp_sweep_once(self.handle))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().asp_stats(self.handle, C.byref(s)))
+        return {n: getattr(s, n) for n, _ in Stats._fields_}
+
+    def state(self, deps_words: int = 0) -> dict:
+        nv = self.n_vars
+        trail = np.zeros(max(nv, 1), np.int32)
+        level = np.zeros(max(nv, 1), np.int32)
+        reason = np.zeros(max(nv, 1), np.uint32)
+        deps = np.zeros((max(nv, 1), max(deps_words, 1)), np.uint64)
+        nt = C.c_int64()
+        _check(lib().asp_debug_state(self.handle, trail.ctypes.data, C.byref(nt), level.ctypes.data,
+                                     reason.ctypes.data, deps.ctypes.data if deps_words else None,
+                                     int(deps_words)))
+        return dict(trail=trail[:nt.value], level=level[:nv], reason=reason[:nv],
+                    deps=deps[:nv] if deps_words else None)
+
+    def nogood(self, nid: int):
+        buf = np.zeros(4096, np.int32)
+        n = lib().asp_debug_nogood(self.handle, int(nid), buf.ctypes.data, 4096)
+        if n < 0:
+            raise AspError(n, lib().asp_last_error().decode())
+        if n > 4096:
+            buf = np.zeros(n, np.int32)
+            lib().asp_debug_nogood(self.handle, int(nid), buf.ctypes.data, n)
+        return buf[:n].copy()
+
+
+def solve_batch(programs, max_models_each: int = 1, cap_each: int = 1):
+    """asp_solve_batch over loaded Programs: (statuses, n_models, models list)."""
+    n = len(programs)
+    handles = (C.c_void_p * n)(*[p.handle.value for p in programs])
+    st = np.zeros(n, np.int32)
+    nm = np.zeros(n, np.int64)
+    bufs = [np.zeros((max(cap_each, 1), max(p.words, 1)), np.uint64) for p in programs]
+    ptrs = (C.c_void_p * n)(*[b.ctypes.data for b in bufs])
+    caps = np.full(n, cap_each, np.int64)
+    _check(lib().asp_solve_batch(n, handles, int(max_models_each), st.ctypes.data, nm.ctypes.data, ptrs,
+                                 caps.ctypes.data))
+    models = [words_to_models(b[:min(int(k), cap_each)], p.n_atoms) for b, k, p in zip(bufs, nm, programs)]
+    return st, nm, models

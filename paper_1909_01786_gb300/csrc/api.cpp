@@ -1,0 +1,579 @@
+// C ABI of libaspgpu: program loading, device memory, launches, results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aspgpu.h"
+#include "device.cuh"
+#include "store.h"
+
+namespace aspgpu {
+cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm);
+cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st);
+}  // namespace aspgpu
+
+using namespace aspgpu;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(ASP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct asp_prog {
+    asp_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_sms = 0;
+    struct Buf { void *p; size_t bytes; };
+    std::vector<Buf> bufs;
+    Dev D{};
+    int grid = 1, block = 1024;
+    size_t smem = 0;
+    int64_t n_nogoods = 0, n_literals = 0, n_units = 0, n_long = 0, store_bytes = 0;
+    bool empty_nogood = false;
+    // internal buffers for the blocking entry points
+    long long *d_result = nullptr;
+    unsigned long long *d_models = nullptr;
+    int64_t d_models_rows = 0;
+    Acc *d_sweep_acc = nullptr;
+};
+
+static void *dalloc(asp_prog *p, size_t bytes)
+{
+    bytes = std::max<size_t>(bytes, 16);
+    void *ptr = nullptr;
+    if (p->opt.dev_alloc) {
+        ptr = p->opt.dev_alloc(bytes, p->opt.alloc_ctx);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) p->bufs.push_back({ptr, bytes});
+    return ptr;
+}
+
+static void release_all(asp_prog *p)
+{
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    for (auto &b : p->bufs) {
+        if (p->opt.dev_free) p->opt.dev_free(b.p, b.bytes, p->opt.alloc_ctx);
+        else cudaFree(b.p);
+    }
+    p->bufs.clear();
+}
+
+template <class T>
+static T *upload(asp_prog *p, const std::vector<T> &v, int &rc)
+{
+    T *d = (T *)dalloc(p, v.size() * sizeof(T));
+    if (!d) { rc = fail(ASP_E_OOM, "device allocation failed"); return nullptr; }
+    if (!v.empty()) {
+        cudaError_t e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "upload"); return nullptr; }
+    }
+    return d;
+}
+
+// Grid size, the static partition of the buckets over the CTAs along groups
+// (an atom with its rules; a constraint), each CTA's slice of auxiliary
+// variables kept in shared memory, and the shared-memory layout.
+static int plan_grid(asp_prog *p, const HostStore &H)
+{
+    Dev &D = p->D;
+    const size_t max_smem = 220 * 1024;
+    const size_t base_smem = 8ull * D.WW + 8ull * 32 + 4ull * 16;
+    int per_sm = 0;
+    cudaError_t e = solve_configure(p->block, max_smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel configuration");
+    if (per_sm < 1) return fail(ASP_E_CUDA, "solver kernel cannot be resident with this block size");
+    const int max_grid = p->n_sms * per_sm;
+    uint64_t total = 0;
+    for (uint64_t x : H.group_lits) total += x;
+    // every SM for any real store; one CTA for tiny programs
+    int64_t want = (int64_t)(total / 2048) + 1;
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>(want, max_grid));
+    if (p->opt.grid_ctas > 0) g = std::min(p->opt.grid_ctas, max_grid);
+    p->grid = g;
+    D.G = (uint32_t)g;
+    // groups [glo[i], glo[i+1]) for CTA i, balanced by literal count
+    const uint32_t ng = (uint32_t)H.n_groups;
+    std::vector<uint32_t> glo(g + 1, ng);
+    glo[0] = 0;
+    {
+        uint64_t acc = 0;
+        int next = 1;
+        for (uint32_t gi = 0; gi < ng && next < g; gi++) {
+            acc += H.group_lits[gi];
+            while (next < g && acc * (uint64_t)g >= total * (uint64_t)next) glo[next++] = gi + 1;
+        }
+        while (next < g) glo[next++] = ng;
+    }
+    const uint32_t G1 = (uint32_t)g + 1;
+    std::vector<uint32_t> boff(16 * (size_t)G1, 0);
+    for (int L = 2; L <= BUCKET_MAX; L++) {
+        const std::vector<uint32_t> &grp = H.bucket_group[L];
+        for (int i = 0; i <= g; i++)
+            boff[L * G1 + i] = (uint32_t)(std::lower_bound(grp.begin(), grp.end(), glo[i]) - grp.begin());
+    }
+    // rules of atom p are [first[p], first[p+1]); their auxiliary variables
+    // are na + 3j .. na + 3j + 2
+    std::vector<uint32_t> first((size_t)D.na + 1, 0);
+    for (uint32_t j = 0; j < D.J; j++) first[H.rule_head[j] + 1]++;
+    for (uint32_t a = 0; a < D.na; a++) first[a + 1] += first[a];
+    std::vector<uint32_t> alo(g), an(g);
+    uint32_t max_an = 0;
+    for (int i = 0; i < g; i++) {
+        uint32_t a0 = std::min(glo[i], D.na), a1 = std::min(glo[i + 1], D.na);
+        uint32_t j0 = first[a0], j1 = first[a1];
+        alo[i] = D.na + 3 * j0;
+        an[i] = 3 * (j1 - j0);
+        max_an = std::max(max_an, an[i]);
+    }
+    size_t atoms_words = (D.na + 15u) / 16u;
+    size_t aux_words = (max_an + 15u) / 16u;
+    D.view_atoms = D.na;
+    if (base_smem + 4 * (atoms_words + aux_words) > max_smem) {
+        // too big for shared memory: keep the auxiliary slice, read atoms globally
+        D.view_atoms = 0;
+        atoms_words = 0;
+        if (base_smem + 4 * aux_words > max_smem) {
+            std::fill(an.begin(), an.end(), 0u);
+            aux_words = 0;
+        }
+    }
+    D.view_words = (uint32_t)(atoms_words + aux_words);
+    p->smem = base_smem + 4 * D.view_words;
+    int rc = ASP_OK;
+    D.cta_boff = upload(p, boff, rc);
+    if (rc == ASP_OK) D.cta_auxlo = upload(p, alo, rc);
+    if (rc == ASP_OK) D.cta_auxn = upload(p, an, rc);
+    if (rc != ASP_OK) return rc;
+    e = solve_configure(p->block, p->smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel configuration");
+    if (per_sm < 1) return fail(ASP_E_CUDA, "solver kernel cannot be resident");
+    return ASP_OK;
+}
+
+extern "C" {
+
+void asp_default_options(asp_options *opt)
+{
+    if (opt) std::memset(opt, 0, sizeof(*opt));
+}
+
+const char *asp_last_error(void) { return g_err.c_str(); }
+
+int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
+                    const int64_t *pos_off, const int32_t *pos,
+                    const int64_t *neg_off, const int32_t *neg,
+                    const asp_options *opt, asp_prog **out)
+{
+    g_err.clear();
+    if (!out) return fail(ASP_E_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(ASP_E_NODEVICE, "no CUDA device");
+    }
+    HostStore H;
+    std::string err;
+    int rc = build_store(n_atoms, n_rules, head, pos_off, pos, neg_off, neg, H, err);
+    if (rc != ASP_OK) return fail(rc, err);
+
+    asp_prog *p = new asp_prog();
+    if (opt) p->opt = *opt;
+    p->stream = (cudaStream_t)p->opt.cuda_stream;
+    cudaGetDevice(&p->device);
+    cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device);
+    p->block = p->opt.block_threads > 0 ? std::min(768, (p->opt.block_threads + 31) / 32 * 32) : 768;
+
+    Dev &D = p->D;
+    D.na = (uint32_t)H.n_atoms;
+    D.J = (uint32_t)H.n_headed;
+    D.nv = (uint32_t)H.n_vars;
+    D.asg_words = (D.nv + 7u) / 8u;
+    D.n_long = (uint32_t)H.long_rel.size();
+    D.n_units = (uint32_t)H.units.size();
+    // literal array: buckets (structure-of-arrays) | long CSR | units | learned
+    std::vector<uint32_t> lits;
+    unsigned long long bucket_lits = 0;
+    for (int L = 2; L <= BUCKET_MAX; L++) {
+        const std::vector<uint32_t> &rows = H.bucket_rows[L];
+        const uint32_t n = (uint32_t)H.bucket_group[L].size();
+        D.bk_base[L] = (uint32_t)lits.size();
+        D.bk_n[L] = n;
+        for (int q = 0; q < L; q++)
+            for (uint32_t k = 0; k < n; k++) lits.push_back(rows[(size_t)k * L + q]);
+        bucket_lits += (unsigned long long)L * n;
+    }
+    std::vector<uint32_t> long_ids(H.long_rel.size());
+    const uint32_t long_base = (uint32_t)lits.size();
+    for (size_t i = 0; i < H.long_rel.size(); i++) long_ids[i] = long_base + H.long_rel[i];
+    lits.insert(lits.end(), H.long_lits.begin(), H.long_lits.end());
+    D.units_base = (uint32_t)lits.size();
+    for (uint32_t u : H.units) lits.push_back(u | END_BIT);
+    D.lits_static = (uint32_t)lits.size();
+    D.static_checks = bucket_lits;
+    int64_t lcap = p->opt.learned_capacity > 0 ? p->opt.learned_capacity
+                                               : std::min<int64_t>(std::max<int64_t>(1 << 22, 4 * (int64_t)lits.size()), 1 << 28);
+    if ((int64_t)D.lits_static + lcap + 128 >= (int64_t)0xFFFFFF00ll) lcap = (int64_t)0xFFFFFF00ll - D.lits_static - 128;
+    D.lits_cap = (uint32_t)(D.lits_static + lcap);
+    D.learned_ng_cap = (uint32_t)std::min<int64_t>(lcap / 2 + 1024, 1 << 28);
+    int levels = p->opt.deps_levels > 0 ? p->opt.deps_levels : 4096;
+    uint32_t WW = (uint32_t)((levels + 63) / 64);
+    uint32_t need = (D.J + 2u + 63u) / 64u;   // deepest possible level is J + 1
+    WW = std::max<uint32_t>(1u, std::min(WW, need));
+    D.WW = WW;
+    D.Wlevels = WW * 64u;
+    D.heuristic = (uint32_t)std::max(0, p->opt.heuristic);
+    p->n_nogoods = H.n_nogoods;
+    p->n_literals = H.n_literals;
+    p->n_units = (int64_t)H.units.size();
+    p->n_long = (int64_t)H.long_rel.size();
+    p->empty_nogood = H.has_empty_nogood;
+    p->store_bytes = (int64_t)D.lits_static * 4;
+
+    rc = ASP_OK;
+    D.lits = (uint32_t *)dalloc(p, ((size_t)D.lits_cap + 128) * 4);
+    if (!D.lits) rc = fail(ASP_E_OOM, "device allocation failed (nogood store)");
+    if (rc == ASP_OK) {
+        cudaError_t e = cudaMemcpyAsync(D.lits, lits.data(), lits.size() * 4, cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "upload store");
+        if (rc == ASP_OK) e = cudaMemsetAsync(D.lits + lits.size(), 0xFF, ((size_t)D.lits_cap + 128 - lits.size()) * 4, p->stream);
+        if (rc == ASP_OK && e != cudaSuccess) rc = cuda_fail(e, "clear learned region");
+    }
+    if (rc == ASP_OK) D.long_ids = upload(p, long_ids, rc);
+    if (rc == ASP_OK) D.rule_head = upload(p, H.rule_head, rc);
+    if (rc == ASP_OK) D.rpos_off = upload(p, H.rpos_off, rc);
+    if (rc == ASP_OK) D.rpos = upload(p, H.rpos, rc);
+    if (rc == ASP_OK) D.rneg_off = upload(p, H.rneg_off, rc);
+    if (rc == ASP_OK) D.rneg = upload(p, H.rneg, rc);
+    if (rc == ASP_OK) D.score = upload(p, H.score, rc);
+    auto alloc = [&](size_t bytes) -> void * {
+        if (rc != ASP_OK) return nullptr;
+        void *q = dalloc(p, bytes);
+        if (!q) rc = fail(ASP_E_OOM, "device allocation failed");
+        return q;
+    };
+    D.learned_ids = (uint32_t *)alloc((size_t)D.learned_ng_cap * 4);
+    D.act = (uint32_t *)alloc((size_t)D.J * 4 + 4);
+    D.asg = (uint32_t *)alloc((size_t)D.asg_words * 4 + 4);
+    D.dl = (int32_t *)alloc((size_t)D.nv * 4 + 4);
+    D.reason = (uint32_t *)alloc((size_t)D.nv * 4 + 4);
+    D.deps = (unsigned long long *)alloc((size_t)D.nv * WW * 8 + 8);
+    D.trail = (uint32_t *)alloc((size_t)D.nv * 4 + 4);
+    D.level_start = (uint32_t *)alloc(((size_t)D.J + 4) * 4);
+    D.dec_var = (uint32_t *)alloc(((size_t)D.J + 4) * 4);
+    D.lm = (uint32_t *)alloc(((size_t)D.na + 31) / 32 * 4 + 4);
+    D.ctl = (Ctl *)alloc(sizeof(Ctl) * 2);
+    D.acc = (Acc *)alloc(sizeof(Acc) * 4);
+    D.stats = (DevStats *)alloc(sizeof(DevStats));
+    D.bar = (Barrier *)alloc(sizeof(Barrier));
+    p->d_result = (long long *)alloc(sizeof(long long) * 4);
+    p->d_sweep_acc = (Acc *)alloc(sizeof(Acc));
+    if (rc == ASP_OK) rc = plan_grid(p, H);
+    if (rc == ASP_OK) {
+        cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(e, "load");
+    }
+    if (rc != ASP_OK) {
+        release_all(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return ASP_OK;
+}
+
+void asp_free(asp_prog *p)
+{
+    if (!p) return;
+    release_all(p);
+    delete p;
+}
+
+}  // extern "C"
+
+// Reset the search state on the stream and set the first control block.
+static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t models_cap,
+                       unsigned long long *d_models, long long *d_result,
+                       uint32_t n_input)
+{
+    Dev &D = p->D;
+    cudaStream_t st = p->stream;
+    cudaError_t e = cudaSuccess;
+    if (mode == MODE_SOLVE) {
+        e = cudaMemsetAsync(D.asg, 0, (size_t)D.asg_words * 4 + 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(D.dl, 0, (size_t)D.nv * 4 + 4, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.act, 0, (size_t)D.J * 4 + 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.stats, 0, sizeof(DevStats), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.bar, 0, sizeof(Barrier), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.level_start, 0, ((size_t)D.J + 4) * 4, st);
+    static thread_local Ctl ctl[2];
+    static thread_local Acc acc[4];
+    std::memset(ctl, 0, sizeof(ctl));
+    ctl[0].op = OP_INIT;
+    ctl[0].cdl = 1;
+    ctl[0].tc = n_input;
+    ctl[0].tb = n_input;
+    ctl[0].lfill = D.lits_static;
+    for (int i = 0; i < 4; i++) {
+        acc[i].ckey = NO_KEY; acc[i].dkey = 0; acc[i].nclaim = 0; acc[i].flag = 0;
+        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D.acc, acc, sizeof(acc), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reset");
+    D.mode = mode;
+    D.max_models = max_models;
+    D.models_cap = models_cap;
+    D.models = d_models;
+    D.result = d_result;
+    D.conflict_budget = p->opt.conflict_budget;
+    D.time_budget_ns = p->opt.time_budget_ms > 0 ? p->opt.time_budget_ms * 1000000ll : 0;
+    return ASP_OK;
+}
+
+static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
+{
+    std::memset(&o, 0, sizeof(o));
+    const Dev &D = p->D;
+    o.n_vars = D.nv; o.n_atoms = D.na; o.n_rules_with_head = D.J;
+    o.n_nogoods = p->n_nogoods; o.n_literals = p->n_literals;
+    o.n_unit_nogoods = p->n_units; o.n_long_nogoods = p->n_long; o.store_bytes = p->store_bytes;
+    o.rounds = (int64_t)s.rounds; o.literal_checks = (int64_t)s.checks; o.propagations = (int64_t)s.props;
+    o.conflicts = (int64_t)s.conflicts; o.decisions = (int64_t)s.decisions; o.completions = (int64_t)s.completions;
+    o.learned = (int64_t)s.learned; o.learned_literals = (int64_t)s.learned_lits; o.loop_nogoods = (int64_t)s.loops;
+    o.models = (int64_t)s.models; o.max_level = (int64_t)s.max_level;
+    o.ns_total = (int64_t)s.ns_total; o.ns_sweep = (int64_t)s.ns_sweep; o.ns_analysis = (int64_t)s.ns_analysis;
+    o.ns_decision = (int64_t)s.ns_decision; o.ns_stability = (int64_t)s.ns_stab;
+}
+
+extern "C" {
+
+int asp_solve_async(asp_prog *p, int64_t max_models, uint64_t *d_models, int64_t models_cap, int64_t *d_result)
+{
+    g_err.clear();
+    if (!p || !d_result || max_models < 0 || models_cap < 0 || (models_cap > 0 && !d_models))
+        return fail(ASP_E_ARG, "bad argument");
+    if (p->empty_nogood) {
+        // a constraint with an empty body: no interpretation satisfies it
+        long long r[4] = {ASP_STATUS_UNSAT, 0, 0, 1};
+        cudaError_t e = cudaMemcpyAsync(d_result, r, sizeof(r), cudaMemcpyHostToDevice, p->stream);
+        return e == cudaSuccess ? ASP_OK : cuda_fail(e, "result");
+    }
+    int rc = reset_state(p, MODE_SOLVE, max_models, models_cap, (unsigned long long *)d_models,
+                         (long long *)d_result, 0);
+    if (rc != ASP_OK) return rc;
+    cudaError_t e = launch_solve(p->D, p->grid, p->block, p->smem, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch");
+    return ASP_OK;
+}
+
+static int finish(asp_prog *p, long long *res)
+{
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "solve");
+    e = cudaMemcpy(res, p->d_result, sizeof(long long) * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "result");
+    return ASP_OK;
+}
+
+int asp_solve(asp_prog *p, int64_t max_models, uint64_t *models, int64_t models_cap,
+              int64_t *n_models, int32_t *status)
+{
+    g_err.clear();
+    if (!p || max_models < 0 || models_cap < 0 || (models_cap > 0 && !models))
+        return fail(ASP_E_ARG, "bad argument");
+    const int64_t words = ((int64_t)p->D.na + 63) / 64;
+    int64_t rows = std::max<int64_t>(models_cap, 1);
+    if (rows > p->d_models_rows) {
+        void *q = dalloc(p, (size_t)(rows * std::max<int64_t>(words, 1)) * 8);
+        if (!q) return fail(ASP_E_OOM, "device allocation failed (models)");
+        p->d_models = (unsigned long long *)q;
+        p->d_models_rows = rows;
+    }
+    int rc = asp_solve_async(p, max_models, (uint64_t *)p->d_models, models_cap, (int64_t *)p->d_result);
+    if (rc != ASP_OK) return rc;
+    long long res[4];
+    if (p->empty_nogood) {
+        cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "solve");
+        if (n_models) *n_models = 0;
+        if (status) *status = ASP_STATUS_UNSAT;
+        return ASP_OK;
+    }
+    rc = finish(p, res);
+    if (rc != ASP_OK) return rc;
+    int64_t got = res[1];
+    int64_t copy = std::min<int64_t>(got, models_cap);
+    if (copy > 0 && words > 0) {
+        cudaError_t e = cudaMemcpy(models, p->d_models, (size_t)(copy * words) * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "models");
+    }
+    if (n_models) *n_models = got;
+    if (status) *status = (int32_t)res[0];
+    if (res[2] != 0) return fail(ASP_E_DEVICE, "device-side error (learned store full or barrier timeout)");
+    if (got > models_cap) return fail(ASP_E_CAPACITY, "more answer sets than model buffer rows");
+    return ASP_OK;
+}
+
+int asp_stats(const asp_prog *p, asp_stats_t *out)
+{
+    if (!p || !out) return fail(ASP_E_ARG, "bad argument");
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "stats sync");
+    DevStats s;
+    e = cudaMemcpy(&s, p->D.stats, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stats");
+    fill_stats(p, s, *out);
+    return ASP_OK;
+}
+
+int asp_debug_propagate(asp_prog *p, const int8_t *partial, int8_t *closure, int32_t *conflict)
+{
+    g_err.clear();
+    if (!p || !partial || !closure) return fail(ASP_E_ARG, "bad argument");
+    const Dev &D = p->D;
+    std::vector<uint32_t> asg(D.asg_words + 1, 0u), trail;
+    std::vector<int32_t> dl(D.nv + 1, 0);
+    std::vector<uint32_t> reason(D.nv + 1, R_INPUT);
+    for (uint32_t v = 0; v < D.nv; v++) {
+        if (partial[v] == 0) continue;
+        uint32_t code = partial[v] > 0 ? V_T : V_F;
+        asg[v >> 3] |= code << ((v & 7u) * 4u);
+        trail.push_back(v);
+        dl[v] = 1;
+    }
+    cudaStream_t st = p->stream;
+    cudaError_t e = cudaMemcpyAsync(p->D.asg, asg.data(), asg.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->D.dl, dl.data(), (size_t)D.nv * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->D.reason, reason.data(), (size_t)D.nv * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !trail.empty())
+        e = cudaMemcpyAsync(p->D.trail, trail.data(), trail.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload partial");
+    int rc = reset_state(p, MODE_PROPAGATE, 0, 0, nullptr, p->d_result, (uint32_t)trail.size());
+    if (rc != ASP_OK) return rc;
+    long long res[4] = {0, 0, 0, 0};
+    if (p->empty_nogood) {
+        res[3] = 1;
+    } else {
+        e = launch_solve(p->D, p->grid, p->block, p->smem, st);
+        if (e != cudaSuccess) return cuda_fail(e, "launch");
+        rc = finish(p, res);
+        if (rc != ASP_OK) return rc;
+    }
+    e = cudaMemcpy(asg.data(), p->D.asg, (size_t)D.asg_words * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "download closure");
+    for (uint32_t v = 0; v < D.nv; v++) {
+        uint32_t c = (asg[v >> 3] >> ((v & 7u) * 4u)) & 3u;
+        closure[v] = c == V_T ? 1 : c == V_F ? -1 : c == 3u ? 2 : 0;
+    }
+    if (conflict) *conflict = (int32_t)res[3];
+    if (res[2] != 0) return fail(ASP_E_DEVICE, "device-side error");
+    return ASP_OK;
+}
+
+int asp_sweep_once(asp_prog *p)
+{
+    if (!p) return fail(ASP_E_ARG, "bad argument");
+    Acc a;
+    a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+    cudaError_t e = cudaMemcpyAsync(p->d_sweep_acc, &a, sizeof(a), cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep reset");
+    e = launch_sweep(p->D, p->d_sweep_acc, p->grid, p->block, p->smem, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    return ASP_OK;
+}
+
+int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *level,
+                    uint32_t *reason, uint64_t *deps, int32_t deps_words)
+{
+    if (!p) return fail(ASP_E_ARG, "bad argument");
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    const Dev &D = p->D;
+    DevStats s;
+    e = cudaMemcpy(&s, D.stats, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "state");
+    int64_t nt = std::min<int64_t>((int64_t)s.pad, (int64_t)D.nv);
+    if (n_trail) *n_trail = nt;
+    if (trail && nt > 0) e = cudaMemcpy(trail, D.trail, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && level) e = cudaMemcpy(level, D.dl, (size_t)D.nv * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reason) e = cudaMemcpy(reason, D.reason, (size_t)D.nv * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && deps && deps_words > 0) {
+        int32_t w = std::min<int32_t>(deps_words, (int32_t)D.WW);
+        e = cudaMemcpy2D(deps, (size_t)deps_words * 8, D.deps, (size_t)D.WW * 8, (size_t)w * 8, D.nv,
+                         cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "state");
+    return ASP_OK;
+}
+
+int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap)
+{
+    if (!p) return fail(ASP_E_ARG, "bad argument");
+    std::vector<uint32_t> buf;
+    if (id & BUCKET_ID) {
+        const uint32_t L = ((id >> 27) & 15u) + 1u, k = id & 0x7FFFFFFu;
+        if (L < 2 || L > (uint32_t)BUCKET_MAX || k >= p->D.bk_n[L]) return fail(ASP_E_ARG, "bad nogood id");
+        for (uint32_t q = 0; q < L; q++) {
+            uint32_t w = 0;
+            cudaError_t e = cudaMemcpy(&w, p->D.lits + p->D.bk_base[L] + (size_t)q * p->D.bk_n[L] + k, 4,
+                                       cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "nogood");
+            if (q < cap) lits[q] = (int32_t)w;
+        }
+        return L;
+    }
+    if (id >= p->D.lits_cap) return fail(ASP_E_ARG, "bad argument");
+    const uint32_t step = 256;
+    const uint64_t alloc_words = (uint64_t)p->D.lits_cap + 128;
+    for (uint64_t off = id; off < alloc_words; off += step) {
+        uint32_t tmp[256];
+        uint32_t n = (uint32_t)std::min<uint64_t>(step, alloc_words - off);
+        cudaError_t e = cudaMemcpy(tmp, p->D.lits + off, (size_t)n * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "nogood");
+        bool done = false;
+        for (uint32_t i = 0; i < n; i++) {
+            buf.push_back(tmp[i] & ~END_BIT);
+            if (tmp[i] & END_BIT) { done = true; break; }
+        }
+        if (done) break;
+    }
+    for (int64_t i = 0; i < (int64_t)buf.size() && i < cap; i++) lits[i] = (int32_t)buf[i];
+    return (int64_t)buf.size();
+}
+
+int asp_solve_batch(int32_t n, asp_prog *const *progs, int64_t max_models_each,
+                    int32_t *statuses, int64_t *n_models, uint64_t *const *models,
+                    const int64_t *models_cap)
+{
+    // sequential fallback over the single-program device loop
+    if (n < 0 || (n > 0 && (!progs || !statuses || !n_models))) return fail(ASP_E_ARG, "bad argument");
+    for (int32_t i = 0; i < n; i++) {
+        int64_t cap = models_cap ? models_cap[i] : 0;
+        uint64_t *m = models ? models[i] : nullptr;
+        int rc = asp_solve(progs[i], max_models_each, m, cap, &n_models[i], &statuses[i]);
+        if (rc != ASP_OK && rc != ASP_E_CAPACITY) return rc;
+    }
+    return ASP_OK;
+}
+
+}  // extern "C"

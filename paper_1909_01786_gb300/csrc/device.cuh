@@ -1,0 +1,107 @@
+// Device-side data layout and small helpers of the solver (internal).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace aspgpu {
+
+// reason markers (anything else is the id of the reason nogood = the offset
+// of its first literal in the literal array)
+constexpr uint32_t R_DECISION = 0xFFFFFFFFu;
+constexpr uint32_t R_COMPLETE = 0xFFFFFFFEu;
+constexpr uint32_t R_INPUT = 0xFFFFFFFDu;
+
+// Assignment: one 4-bit code per variable, 8 per 32-bit word.
+//   bit 0: true, bit 1: false, bit 2 / bit 3: claimed in an even / odd
+//   round and not yet committed ("fresh").  A fresh variable reads as
+//   unassigned during the round that claimed it, so every sweep classifies
+//   nogoods against the assignment as it stood when the round began (plus
+//   clash detection through the atomic claim), and dependency bitmaps are
+//   only ever computed from committed variables.
+constexpr uint32_t V_T = 1u, V_F = 2u;
+
+enum Op : uint32_t {
+    OP_INIT = 1,      // InitialPropagation: apply the unit nogoods at level 1
+    OP_ROUND,         // commit last round's claims, then propagate-and-check sweep
+    OP_APPLY,         // apply the chosen decision (or complete the assignment) + sweep
+    OP_BACKJUMP,      // unassign every trail entry above the target level
+    OP_STAB_INIT,     // stability check: clear the least-model bitset
+    OP_STAB_ITER,     // one pass of the immediate-consequence operator of the reduct
+    OP_STAB_RESULT,   // answer set found -> record it and block it; else loop nogood
+    OP_ANALYZE_ID,    // conflict analysis of the loop nogood just written
+    OP_DONE
+};
+
+enum Mode : uint32_t { MODE_SOLVE = 0, MODE_PROPAGATE = 1 };
+
+constexpr unsigned long long NO_KEY = ~0ull;
+
+struct Ctl {              // double-buffered control block (phase parity)
+    uint32_t op, cdl, tc, tb;   // tc: trail entries committed; tb: base of last claims
+    // (a claim's level, reason and dependency bitmap are written when it is
+    // made; "committing" only clears its fresh bit and makes it visible to
+    // every CTA's shared-memory view)
+    uint32_t round, clean, target, conf_id;
+    uint32_t n_learned, lfill, stab_first, idle_completes;
+    long long n_models;
+    int32_t status, err;
+    int32_t conflict, pad;
+};
+
+struct Acc {              // per-phase accumulators, indexed by phase % 4
+    unsigned long long ckey;    // min over conflicts of (length << 32 | nogood id)
+    unsigned long long dkey;    // max over candidate rules of (score << 32 | ~j)
+    uint32_t nclaim;            // variables claimed in the phase
+    uint32_t flag;              // something changed (least-model iteration)
+    uint32_t minU;              // smallest unfounded true atom
+    uint32_t nlits;             // literals appended to the loop nogood
+    unsigned long long checks;  // literals classified by long/learned sweeps
+};
+
+struct DevStats {
+    unsigned long long rounds, checks, props, conflicts, decisions, completions;
+    unsigned long long learned, learned_lits, loops, models, max_level;
+    unsigned long long ns_total, ns_sweep, ns_analysis, ns_decision, ns_stab;
+    unsigned long long phases, pad;
+};
+
+struct Barrier { unsigned int count, gen, err, pad; };
+
+struct Dev {
+    uint32_t na, J, nv, asg_words;
+    uint32_t n_long, n_units, units_base, pad1;
+    // bucket L (2..15): literal q of nogood k at lits[bk_base[L] + q*bk_n[L] + k]
+    uint32_t bk_base[16], bk_n[16];
+    uint32_t lits_static, lits_cap, learned_ng_cap, pad0;
+    uint32_t WW, Wlevels, mode, heuristic;
+    // static partition of the buckets over the CTAs by groups (atoms and
+    // their rules; constraints): CTA g owns nogoods [cta_boff[L*(G+1)+g],
+    // cta_boff[L*(G+1)+g+1]) of bucket L, and keeps in shared memory the
+    // atoms [0, view_atoms) and the auxiliary variables
+    // [cta_auxlo, cta_auxlo + cta_auxn) those nogoods refer to
+    uint32_t G, view_atoms, view_words, pad2;
+    const uint32_t *cta_boff;    // [16 * (G+1)]
+    const uint32_t *cta_auxlo;   // [G]
+    const uint32_t *cta_auxn;    // [G]
+    long long max_models, models_cap, conflict_budget, time_budget_ns;
+    unsigned long long static_checks;    // literals of the buckets (read every sweep)
+    uint32_t *lits;                      // buckets | long | units | learned
+    const uint32_t *long_ids;
+    uint32_t *learned_ids;
+    const int32_t *rule_head;
+    const uint32_t *rpos_off, *rpos, *rneg_off, *rneg, *score;
+    uint32_t *act;
+    uint32_t *asg;
+    int32_t *dl;
+    uint32_t *reason;
+    unsigned long long *deps;
+    uint32_t *trail, *level_start, *dec_var, *lm;
+    Ctl *ctl;
+    Acc *acc;
+    DevStats *stats;
+    Barrier *bar;
+    unsigned long long *models;
+    long long *result;
+};
+
+}  // namespace aspgpu

@@ -1,0 +1,1125 @@
+// Device-resident conflict-driven answer-set search (sm_103a).
+//
+// One persistent cooperative kernel runs the whole loop of Algorithm 1:
+// InitialPropagation, propagate-and-check sweeps to fixpoint (Section 4.1),
+// fwd-learning from decision-level dependency bitmaps (Section 4.2,
+// Algorithm 4), Backjump, Decision over applicable rules (Section 2),
+// CompleteAssignment, and the stability step.  Phases are separated by a
+// grid barrier; the leader (CTA 0, thread 0) writes the control block for the
+// next phase into the other half of a double buffer, so all CTAs read a
+// stable copy while it is being updated.
+//
+// Sweep design.  The static nogoods sit in one bucket per exact length
+// (Section 4: one kernel per length class), stored structure-of-arrays, and
+// are cut into contiguous ranges, one per CTA, along groups of nogoods (an
+// atom's rules and the atom's own nogood).  Each CTA keeps a 2-bit view of
+// the assignment in shared memory: all atoms, plus the auxiliary variables
+// of the rules its ranges refer to.  One lane classifies one nogood against
+// that view.  A claim (atomicOr on the global 4-bit codes) computes the
+// claimed variable's dependency bitmap at once, from its reason, and is then
+// published in the CTA's own view, so chains of implications inside a CTA
+// can resolve within one sweep; other CTAs see the claim after the next
+// barrier.  Long and learned nogoods are classified by one warp each (ballot
+// and popc over lanes), against the global codes.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "device.cuh"
+#include "store.h"
+
+namespace aspgpu {
+
+#define FULL_MASK 0xFFFFFFFFu
+
+// ------------------------------------------------------------ primitives
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier with a bounded wait: returns false (and sets the sticky error
+// flag) if the other CTAs do not arrive within ~20 s.
+__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (nblocks > 1) {
+            unsigned g = ld_acquire_u32(&b->gen);
+            __threadfence();
+            unsigned arrived = atomicAdd(&b->count, 1u);
+            if (arrived == nblocks - 1) {
+                atomicExch(&b->count, 0u);
+                __threadfence();
+                atomicAdd(&b->gen, 1u);
+            } else {
+                unsigned long long t0 = globaltimer_ns();
+                unsigned spins = 0;
+                while (ld_acquire_u32(&b->gen) == g) {
+                    if (ld_acquire_u32(&b->err)) { ok = 0; break; }
+                    if ((++spins & 1023u) == 0 && globaltimer_ns() - t0 > 20000000000ull) {
+                        atomicExch(&b->err, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (ld_acquire_u32(&b->err)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ uint32_t nib(uint32_t word, uint32_t v) { return (word >> ((v & 7u) * 4u)) & 0xFu; }
+
+// effective value during a round: fresh variables (claimed this round) read
+// as unassigned
+__device__ __forceinline__ uint32_t eff_val(uint32_t code, uint32_t fresh_cur)
+{
+    return (code & fresh_cur) ? 0u : (code & 3u);
+}
+
+__device__ __forceinline__ uint32_t global_val(const Dev &D, uint32_t v, uint32_t fresh_cur)
+{
+    return eff_val(nib(__ldcg(D.asg + (v >> 3)), v), fresh_cur);
+}
+
+// words of a dependency bitmap that can be non-zero for a variable at level L
+__device__ __forceinline__ uint32_t deps_words(const Dev &D, uint32_t L)
+{
+    uint32_t w = (L + 63u) >> 6;
+    return w < D.WW ? w : D.WW;
+}
+
+// bit of level L (levels >= Wlevels share the overflow bit Wlevels-1)
+__device__ __forceinline__ uint32_t level_bit(const Dev &D, uint32_t L)
+{
+    return L < D.Wlevels ? L - 1u : D.Wlevels - 1u;
+}
+
+__device__ __forceinline__ uint32_t lit_at(const Dev &D, uint32_t idx)
+{
+    return idx < D.lits_static ? __ldg(D.lits + idx) : __ldcg(D.lits + idx);
+}
+
+// literal q (without end flag) and length of nogood `id`
+__device__ __forceinline__ uint32_t ng_lit(const Dev &D, uint32_t id, uint32_t q)
+{
+    if (id & BUCKET_ID) {
+        const uint32_t L = ((id >> 27) & 15u) + 1u, k = id & 0x7FFFFFFu;
+        return __ldg(D.lits + D.bk_base[L] + (size_t)q * D.bk_n[L] + k);
+    }
+    return lit_at(D, id + q) & ~END_BIT;
+}
+
+__device__ __forceinline__ uint32_t ng_len(const Dev &D, uint32_t id)
+{
+    if (id & BUCKET_ID) return ((id >> 27) & 15u) + 1u;
+    uint32_t n = 1;
+    while (!(lit_at(D, id + n - 1u) & END_BIT)) n++;
+    return n;
+}
+
+// ---------------------------------------------------------------- views
+
+// The CTA's 2-bit view (0 unassigned, 1 true, 2 false) of the atoms
+// [0, na_v) and of the auxiliary variables [auxlo, auxlo + auxn), which
+// follow the atoms at entry aux_base (a multiple of 16).
+struct View {
+    volatile uint32_t *w;
+    uint32_t na_v, aux_base, auxlo, auxn;
+
+    // entry of v in the view, or 0xFFFFFFFF if v is not in it
+    __device__ __forceinline__ uint32_t index(uint32_t v) const
+    {
+        if (v < na_v) return v;
+        uint32_t k = v - auxlo;
+        return k < auxn ? aux_base + k : 0xFFFFFFFFu;
+    }
+};
+
+__device__ __forceinline__ uint32_t view_val(const Dev &D, const View &V, uint32_t v, uint32_t fresh_cur)
+{
+    uint32_t i = V.index(v);
+    if (i != 0xFFFFFFFFu) return (V.w[i >> 4] >> (2u * (i & 15u))) & 3u;
+    return global_val(D, v, fresh_cur);
+}
+
+__device__ __forceinline__ bool view_set(const View &V, uint32_t v, uint32_t val)
+{
+    uint32_t i = V.index(v);
+    if (i == 0xFFFFFFFFu) return false;
+    uint32_t sh = 2u * (i & 15u);
+    uint32_t old = atomicOr((uint32_t *)(V.w + (i >> 4)), val << sh);
+    return ((old >> sh) & 3u) == 0u;
+}
+
+__device__ __forceinline__ void view_clear(const View &V, uint32_t v)
+{
+    uint32_t i = V.index(v);
+    if (i != 0xFFFFFFFFu) atomicAnd((uint32_t *)(V.w + (i >> 4)), ~(3u << (2u * (i & 15u))));
+}
+
+// 2-bit effective values of the 8 variables of one global code word
+__device__ __forceinline__ uint32_t pack8(uint32_t word, uint32_t fresh_cur)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 8u; q++) m |= eff_val((word >> (4u * q)) & 0xFu, fresh_cur) << (2u * q);
+    return m;
+}
+
+// Rebuild the whole view from the global codes (fresh claims read as
+// unassigned); one view word holds 16 variables = two global code words.
+__device__ __forceinline__ void view_reload(const Dev &D, const View &V, uint32_t fresh_cur)
+{
+    const uint32_t wa = (V.na_v + 15u) >> 4, wx = (V.auxn + 15u) >> 4;
+    for (uint32_t k = threadIdx.x; k < wa; k += blockDim.x) {
+        uint32_t lo = __ldcg(D.asg + 2u * k), hi = 2u * k + 1u < D.asg_words ? __ldcg(D.asg + 2u * k + 1u) : 0u;
+        uint32_t m = pack8(lo, fresh_cur) | (pack8(hi, fresh_cur) << 16);
+        uint32_t valid = V.na_v - 16u * k;    // entries of this word that are atoms
+        if (valid < 16u) m &= (1u << (2u * valid)) - 1u;
+        V.w[k] = m;
+    }
+    for (uint32_t k = threadIdx.x; k < wx; k += blockDim.x) {
+        // variables auxlo + 16k .. +15: spread over up to three code words
+        const uint32_t v0 = V.auxlo + 16u * k;
+        const uint32_t w0 = v0 >> 3, sh = v0 & 7u;
+        uint32_t a = __ldcg(D.asg + w0);
+        uint32_t b = w0 + 1u < D.asg_words ? __ldcg(D.asg + w0 + 1u) : 0u;
+        uint32_t c = w0 + 2u < D.asg_words ? __ldcg(D.asg + w0 + 2u) : 0u;
+        // 24 nibbles starting at a; take 16 from nibble sh
+        unsigned long long lo64 = ((unsigned long long)b << 32) | a;
+        uint32_t first8 = (uint32_t)(lo64 >> (4u * sh));
+        unsigned long long hi64 = ((unsigned long long)c << 32) | b;
+        uint32_t next8 = (uint32_t)(hi64 >> (4u * sh));
+        uint32_t m = pack8(first8, fresh_cur) | (pack8(next8, fresh_cur) << 16);
+        uint32_t valid = V.auxn - 16u * k;
+        if (valid < 16u) m &= (1u << (2u * valid)) - 1u;
+        V.w[V.aux_base / 16u + k] = m;
+    }
+}
+
+// ---------------------------------------------------------------- claims
+
+// Claim the complement of an unassigned literal: 0 won, 1 agreed, 2 clash.
+__device__ __forceinline__ int claim_var(uint32_t *asg, uint32_t v, uint32_t valbit, uint32_t fresh_cur)
+{
+    uint32_t sh = (v & 7u) * 4u;
+    uint32_t old = atomicOr(asg + (v >> 3), (valbit | fresh_cur) << sh);
+    uint32_t ov = (old >> sh) & 3u;
+    if (ov == 0u) return 0;
+    if (ov & valbit) return 1;
+    return 2;
+}
+
+struct SweepCtx {
+    const Dev *D;
+    View V;
+    uint32_t fresh;        // fresh bit of the current round
+    uint32_t cdl;          // level of new claims
+    uint32_t tbase;        // trail index of this phase's first claim
+    Acc *acc;              // this phase's accumulators
+    bool do_claim;
+    bool use_view;
+    uint32_t dec_v;        // decision variable set in this phase (its level
+                           // and bitmap are known here before they reach memory)
+};
+
+__device__ __forceinline__ void report_conflict(const SweepCtx &X, uint32_t id, uint32_t len)
+{
+    atomicMin(&X.acc->ckey, ((unsigned long long)len << 32) | id);
+}
+
+// Record a won claim: trail slot, level, reason.
+__device__ __forceinline__ void record_claim(const SweepCtx &X, uint32_t v, uint32_t id)
+{
+    const Dev &D = *X.D;
+    uint32_t pos = X.tbase + atomicAdd(&X.acc->nclaim, 1u);
+    if (pos < D.nv) D.trail[pos] = v;
+    D.dl[v] = (int32_t)X.cdl;
+    D.reason[v] = id;
+}
+
+// One lane per literal u of a reason (has = false on lanes holding none):
+// the warp ORs Deps[u] over lanes with level > 1 and writes Deps[x]
+// (Section 4.2, mk_dl_bitmap).  All 32 lanes call it.
+__device__ __forceinline__ void warp_or_deps(const SweepCtx &X, bool has, uint32_t u, uint32_t x,
+                                             int writer, bool accumulate)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t L = X.cdl;
+    const uint32_t nw = deps_words(D, L);
+    const bool is_dec = has && u == X.dec_v;
+    int32_t Lu = !has ? 0 : is_dec ? (int32_t)L : __ldcg(D.dl + u);
+    uint32_t nwu = (has && Lu > 1) ? deps_words(D, (uint32_t)Lu) : 0u;
+    const uint32_t dbit = level_bit(D, L);
+    for (uint32_t w = 0; w < nw; w++) {
+        unsigned long long c = w >= nwu ? 0ull
+                             : is_dec ? (w == (dbit >> 6) ? (1ull << (dbit & 63u)) : 0ull)
+                             : __ldcg(D.deps + (size_t)u * D.WW + w);
+        unsigned lo = __reduce_or_sync(FULL_MASK, (unsigned)c);
+        unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(c >> 32));
+        if ((int)lane == writer) {
+            unsigned long long m = ((unsigned long long)hi << 32) | lo;
+            unsigned long long *dst = D.deps + (size_t)x * D.WW + w;
+            *dst = accumulate ? (__ldcg(dst) | m) : m;
+        }
+    }
+}
+
+// value of a literal's variable during the sweep (view, else global codes)
+__device__ __forceinline__ uint32_t lit_val(const SweepCtx &X, uint32_t l)
+{
+    return X.use_view ? view_val(*X.D, X.V, l >> 1, X.fresh) : global_val(*X.D, l >> 1, X.fresh);
+}
+
+// Dependency bitmap of x from the other literals of one lane's nogood (lit),
+// OR over those with level > 1 (Section 4.2, mk_dl_bitmap).
+template <int L>
+__device__ __forceinline__ void lane_deps(const SweepCtx &X, const uint32_t (&lit)[L], uint32_t x)
+{
+    const Dev &D = *X.D;
+    const uint32_t nw = deps_words(D, X.cdl);
+    const uint32_t dbit = level_bit(D, X.cdl);
+    int32_t Lu[L];
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+        uint32_t u = lit[q] >> 1;
+        Lu[q] = (u == x) ? 0 : (u == X.dec_v) ? (int32_t)X.cdl : __ldcg(D.dl + u);
+    }
+    for (uint32_t w = 0; w < nw; w++) {
+        unsigned long long acc = 0;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+            uint32_t u = lit[q] >> 1;
+            if (Lu[q] > 1 && w < deps_words(D, (uint32_t)Lu[q]))
+                acc |= (u == X.dec_v) ? (w == (dbit >> 6) ? (1ull << (dbit & 63u)) : 0ull)
+                                      : __ldcg(D.deps + (size_t)u * D.WW + w);
+        }
+        D.deps[(size_t)x * D.WW + w] = acc;
+    }
+}
+
+// U groups of 32 nogoods of bucket L, lane = nogood k0 + t*stride + lane.
+// All literals are loaded (coalesced, one row per literal position) and
+// their values gathered before any is classified: a nogood is satisfied if
+// some literal's complement holds, violated if all hold, unit if exactly one
+// is unassigned and the rest hold (Section 2).  Repeats while a claim of
+// this warp changed the view.
+template <int L, int U>
+__device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uint32_t k1, uint32_t stride)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t *base = D.lits + D.bk_base[L];
+    const uint32_t n = D.bk_n[L];
+    uint32_t lit[U][L];
+#pragma unroll
+    for (int t = 0; t < U; t++) {
+        const uint32_t k = k0 + (uint32_t)t * stride + lane;
+#pragma unroll
+        for (int q = 0; q < L; q++) lit[t][q] = k < k1 ? __ldg(base + (size_t)q * n + k) : PAD_LIT;
+    }
+    for (int pass = 0; pass < 8; pass++) {
+        uint32_t val[U][L];
+#pragma unroll
+        for (int t = 0; t < U; t++)
+#pragma unroll
+            for (int q = 0; q < L; q++) val[t][q] = lit[t][q] == PAD_LIT ? 0u : lit_val(X, lit[t][q]);
+        bool pub = false;
+#pragma unroll
+        for (int t = 0; t < U; t++) {
+            const uint32_t k = k0 + (uint32_t)t * stride + lane;
+            if (k >= k1) continue;
+            bool sat = false;
+            uint32_t n_un = 0, ul = 0;
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+                uint32_t v = val[t][q];
+                sat |= v == ((lit[t][q] & 1u) ? V_T : V_F);
+                if (v == 0u) { n_un++; ul = lit[t][q]; }
+            }
+            if (sat || n_un > 1u) continue;
+            const uint32_t id = bucket_nogood_id((uint32_t)L, k);
+            if (n_un == 0u) { report_conflict(X, id, (uint32_t)L); continue; }
+            if (!X.do_claim) { atomicAdd(&X.acc->flag, 1u); continue; }
+            const uint32_t x = ul >> 1, valbit = (ul & 1u) ? V_T : V_F;
+            const int r = claim_var(D.asg, x, valbit, X.fresh);
+            if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
+            if (r != 0) continue;
+            record_claim(X, x, id);
+            if (X.cdl > 1u) lane_deps<L>(X, lit[t], x);
+            if (X.use_view) {
+                __threadfence_block();
+                pub |= view_set(X.V, x, valbit);
+            }
+        }
+        if (!X.use_view || !X.do_claim || !__any_sync(FULL_MASK, pub)) break;
+    }
+}
+
+template <int L, int U>
+__device__ __forceinline__ void run_bucket(const SweepCtx &X, uint32_t b0, uint32_t b1)
+{
+    const uint32_t wid = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const uint32_t ntask = (b1 - b0 + 31u) >> 5;
+    for (uint32_t t0 = wid; t0 < ntask; t0 += nwb * (uint32_t)U)
+        bucket_tasks<L, U>(X, b0 + t0 * 32u, b1, nwb * 32u);
+}
+
+// A nogood of any length, one warp, lanes over literals (ballot/popc),
+// stopping once it is satisfied or has two unassigned literals; literals are
+// checked against the global codes, 128 at a time (four loads and their
+// gathers in flight before the first ballot).
+__device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, unsigned long long &checks)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    bool any_opp = false, done = false;
+    uint32_t n_un = 0, ulit = 0, len = 0;
+    for (uint32_t off = id; !done && off < D.lits_cap; off += 128u) {
+        uint32_t w[4], code[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) w[q] = lit_at(D, off + 32u * q + lane);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uint32_t v = (w[q] & ~END_BIT) >> 1;
+            code[q] = v < D.nv ? nib(__ldcg(D.asg + (v >> 3)), v) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (done) break;
+            unsigned Bend = __ballot_sync(FULL_MASK, (w[q] & END_BIT) != 0u);
+            unsigned valid = Bend ? ((2u << (__ffs(Bend) - 1)) - 1u) : FULL_MASK;
+            uint32_t l = w[q] & ~END_BIT;
+            bool mine = ((valid >> lane) & 1u) && (l >> 1) < D.nv;
+            uint32_t val = mine ? eff_val(code[q], X.fresh) : 0u;
+            bool opp = mine && val == ((l & 1u) ? V_T : V_F);
+            bool un = mine && val == 0u;
+            unsigned Bopp = __ballot_sync(FULL_MASK, opp);
+            unsigned Bun = __ballot_sync(FULL_MASK, un);
+            uint32_t first_un = __shfl_sync(FULL_MASK, l, Bun ? __ffs(Bun) - 1 : 0);
+            if (Bun && n_un == 0) ulit = first_un;
+            n_un += (uint32_t)__popc(Bun);
+            len += (uint32_t)__popc(valid);
+            checks += (uint32_t)__popc(valid);
+            if (Bopp) { any_opp = true; done = true; }
+            else if (Bend || n_un > 1) done = true;
+        }
+    }
+    if (any_opp) return;
+    int won = 0;
+    if (lane == 0) {
+        if (n_un == 0) {
+            report_conflict(X, id, len);
+        } else if (n_un == 1) {
+            if (!X.do_claim) {
+                atomicAdd(&X.acc->flag, 1u);
+            } else {
+                uint32_t v = ulit >> 1, valbit = (ulit & 1u) ? V_T : V_F;
+                int r = claim_var(D.asg, v, valbit, X.fresh);
+                if (r == 0) { record_claim(X, v, id); won = 1; }
+                else if (r == 2) report_conflict(X, id, len);
+            }
+        }
+    }
+    won = __shfl_sync(FULL_MASK, won, 0);
+    if (!won) return;
+    const uint32_t x = ulit >> 1;
+    if (X.cdl > 1u) {
+        __threadfence_block();
+        bool first = true;
+        for (uint32_t off = id; off < D.lits_cap; off += 32u) {
+            uint32_t w2 = lit_at(D, off + lane);
+            unsigned Bend = __ballot_sync(FULL_MASK, (w2 & END_BIT) != 0u);
+            unsigned valid = Bend ? ((2u << (__ffs(Bend) - 1)) - 1u) : FULL_MASK;
+            uint32_t u2 = (w2 & ~END_BIT) >> 1;
+            bool has = ((valid >> lane) & 1u) && u2 != x && u2 < D.nv;
+            warp_or_deps(X, has, u2, x, 0, !first);
+            first = false;
+            if (Bend) break;
+        }
+    }
+    if (lane == 0 && X.use_view) {
+        __threadfence_block();
+        view_set(X.V, x, (ulit & 1u) ? V_T : V_F);
+    }
+}
+
+// Propagate-and-check over this CTA's ranges of every bucket, then
+// (grid-wide) the static long nogoods and the learned nogoods.
+__device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t G1 = D.G + 1u;
+#pragma unroll 1
+    for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
+        const uint32_t b0 = __ldg(D.cta_boff + L * G1 + blockIdx.x);
+        const uint32_t b1 = __ldg(D.cta_boff + L * G1 + blockIdx.x + 1u);
+        if (b1 <= b0) continue;
+        switch (L) {
+        case 2: run_bucket<2, 4>(X, b0, b1); break;
+        case 3: run_bucket<3, 2>(X, b0, b1); break;
+        case 4: run_bucket<4, 2>(X, b0, b1); break;
+        case 5: run_bucket<5, 1>(X, b0, b1); break;
+        case 6: run_bucket<6, 1>(X, b0, b1); break;
+        case 7: run_bucket<7, 1>(X, b0, b1); break;
+        case 8: run_bucket<8, 1>(X, b0, b1); break;
+        case 9: run_bucket<9, 1>(X, b0, b1); break;
+        case 10: run_bucket<10, 1>(X, b0, b1); break;
+        case 11: run_bucket<11, 1>(X, b0, b1); break;
+        case 12: run_bucket<12, 1>(X, b0, b1); break;
+        case 13: run_bucket<13, 1>(X, b0, b1); break;
+        case 14: run_bucket<14, 1>(X, b0, b1); break;
+        default: run_bucket<15, 1>(X, b0, b1); break;
+        }
+    }
+    unsigned long long checks = 0;
+    const uint32_t nl = D.n_long + n_learned;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gwarp; i < nl; i += nwarps) {
+        uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
+        classify_long(X, id, checks);
+    }
+    if (lane == 0 && checks) atomicAdd(&X.acc->checks, checks);
+}
+
+// bitmap word w of "every decision level 2..L" (CompleteAssignment reading)
+__device__ __forceinline__ unsigned long long all_levels_word(const Dev &D, uint32_t L, uint32_t w)
+{
+    // exact bits 1 .. min(L, Wlevels-1)-1, plus overflow if L >= Wlevels
+    uint32_t hi = (L < D.Wlevels ? L : D.Wlevels - 1u);   // exclusive upper bit
+    unsigned long long m = 0;
+    uint32_t lo_bit = w * 64u, hi_bit = lo_bit + 64u;
+    uint32_t a = lo_bit > 1u ? lo_bit : 1u, b = hi_bit < hi ? hi_bit : hi;
+    if (a < b) {
+        uint32_t n = b - a;
+        unsigned long long ones = n >= 64u ? ~0ull : ((1ull << n) - 1ull);
+        m = ones << (a - lo_bit);
+    }
+    if (L >= D.Wlevels && w == D.WW - 1u) m |= 1ull << 63;
+    return m;
+}
+
+// OR of the dependency bitmaps of the literals of nogood `id` other than
+// variable `skip` with level > 1, word w.
+__device__ __forceinline__ unsigned long long or_deps_word(const Dev &D, uint32_t id, uint32_t skip, uint32_t w)
+{
+    unsigned long long acc = 0;
+    const uint32_t len = ng_len(D, id);
+    for (uint32_t q = 0; q < len; q++) {
+        uint32_t u = ng_lit(D, id, q) >> 1;
+        if (u == skip) continue;
+        int32_t L = __ldcg(D.dl + u);
+        if (L > 1 && w < deps_words(D, (uint32_t)L)) acc |= __ldcg(D.deps + (size_t)u * D.WW + w);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ unsigned long long shfl_max_u64(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_down_sync(FULL_MASK, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+struct Smem {
+    unsigned long long *bm;     // [WW] conflict bitmap
+    unsigned long long *red;    // [32]
+    uint32_t *misc;             // [16]
+};
+
+// Decision (Section 2 / Section 4): among rules whose head is unassigned,
+// with t_r true, n_r not false and b_r unassigned (applicable), pick the
+// highest score, ties to the lowest rule index.
+__device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, uint32_t gtid, uint32_t nthreads)
+{
+    unsigned long long best = 0;
+    for (uint32_t j = gtid; j < D.J; j += nthreads) {
+        uint32_t h = (uint32_t)__ldg(D.rule_head + j);
+        uint32_t b = D.na + 3u * j, t = b + 1u, n = b + 2u;
+        uint32_t ch = nib(__ldcg(D.asg + (h >> 3)), h) & 3u;
+        uint32_t cb = nib(__ldcg(D.asg + (b >> 3)), b) & 3u;
+        uint32_t ct = nib(__ldcg(D.asg + (t >> 3)), t) & 3u;
+        uint32_t cn = nib(__ldcg(D.asg + (n >> 3)), n) & 3u;
+        if (ch == 0u && cb == 0u && ct == V_T && cn != V_F) {
+            unsigned long long sc = __ldg(D.score + j);
+            if (D.heuristic == 1) sc += (unsigned long long)__ldcg(D.act + j) * 8ull;
+            if (sc > 0x7FFFFFFFull) sc = 0x7FFFFFFFull;
+            unsigned long long key = ((sc + 1ull) << 32) | (0xFFFFFFFFull - j);
+            best = key > best ? key : best;
+        }
+    }
+    best = shfl_max_u64(best);
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    if (lane == 0) S.red[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long x = lane < (blockDim.x >> 5) ? S.red[lane] : 0ull;
+        x = shfl_max_u64(x);
+        if (lane == 0 && x) atomicMax(&acc->dkey, x);
+    }
+}
+
+// fwd-learning (Algorithm 4) on CTA 0: OR the dependency bitmaps of the
+// conflict's literals (plus those of the clashing variable's reason), take
+// the highest level involved, and learn the nogood made of the decision
+// literals of the levels in the bitmap.  Returns via S.misc:
+//   misc[0] = 1 if the bitmap is empty (conflict at the root),
+//   misc[1] = backjump target, misc[2] = learned length.
+__device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g, uint32_t cdl, uint32_t lfill, bool find_clash)
+{
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t nw = deps_words(D, cdl);
+    for (uint32_t w = tid; w < D.WW; w += nt) S.bm[w] = 0ull;
+    if (tid == 0) {
+        // length of g and the clashing variable: the one with both values set
+        uint32_t len = ng_len(D, g), clash = 0xFFFFFFFFu;
+        for (uint32_t q = 0; q < len && find_clash; q++) {
+            uint32_t u = ng_lit(D, g, q) >> 1;
+            if ((nib(__ldcg(D.asg + (u >> 3)), u) & 3u) == 3u) clash = u;
+        }
+        S.misc[4] = len;
+        S.misc[5] = clash;
+    }
+    __syncthreads();
+    const uint32_t len = S.misc[4], clash = S.misc[5];
+    for (uint32_t t = tid; t < len * nw; t += nt) {
+        uint32_t i = t / nw, w = t % nw;
+        uint32_t u = ng_lit(D, g, i) >> 1;
+        if (u == clash) continue;
+        int32_t L = __ldcg(D.dl + u);
+        if (L > 1 && w < deps_words(D, (uint32_t)L)) atomicOr(&S.bm[w], __ldcg(D.deps + (size_t)u * D.WW + w));
+    }
+    if (clash != 0xFFFFFFFFu) {
+        uint32_t r = __ldcg(D.reason + clash);
+        if (r == R_COMPLETE) {
+            for (uint32_t w = tid; w < nw; w += nt) atomicOr(&S.bm[w], all_levels_word(D, cdl, w));
+        } else if (r < R_INPUT) {
+            for (uint32_t w = tid; w < nw; w += nt) atomicOr(&S.bm[w], or_deps_word(D, r, clash, w));
+        } else if (r == R_DECISION) {
+            int32_t L = __ldcg(D.dl + clash);
+            for (uint32_t w = tid; w < nw; w += nt)
+                if (L > 1 && w < deps_words(D, (uint32_t)L)) atomicOr(&S.bm[w], __ldcg(D.deps + (size_t)clash * D.WW + w));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        bool overflow = cdl >= D.Wlevels && (S.bm[D.WW - 1] >> 63);
+        int top = -1;
+        for (int w = (int)nw - 1; w >= 0 && top < 0; w--) {
+            unsigned long long m = S.bm[w];
+            if (w == (int)D.WW - 1) m &= ~(1ull << 63);
+            if (m) top = w * 64 + 63 - __clzll((long long)m);
+        }
+        if (!overflow && top < 0) {
+            S.misc[0] = 1;
+        } else {
+            uint32_t h = overflow ? cdl : (uint32_t)top + 1u;
+            S.misc[0] = 0;
+            S.misc[1] = h - 1u;
+            // write the decision literals, levels ascending
+            uint32_t n = 0;
+            for (uint32_t w = 0; w < nw; w++) {
+                unsigned long long m = S.bm[w];
+                if (w == D.WW - 1u) m &= ~(1ull << 63);
+                while (m) {
+                    uint32_t bit = (uint32_t)__ffsll((long long)m) - 1u;
+                    m &= m - 1ull;
+                    uint32_t level = w * 64u + bit + 1u;
+                    if (level < 2u || level > cdl) continue;
+                    uint32_t pos = lfill + n;
+                    if (pos + 1u < D.lits_cap) D.lits[pos] = mk_lit(__ldcg(D.dec_var + level), false);
+                    n++;
+                }
+            }
+            if (overflow) {
+                for (uint32_t level = D.Wlevels; level <= cdl; level++) {
+                    uint32_t pos = lfill + n;
+                    if (pos + 1u < D.lits_cap) D.lits[pos] = mk_lit(__ldcg(D.dec_var + level), false);
+                    n++;
+                }
+            }
+            if (n > 0 && lfill + n < D.lits_cap) D.lits[lfill + n - 1u] |= END_BIT;
+            S.misc[2] = n;
+            if (D.heuristic == 1) {
+                for (uint32_t q = 0; q < n && lfill + q < D.lits_cap; q++) {
+                    uint32_t bv = (D.lits[lfill + q] & ~END_BIT) >> 1;
+                    if (bv >= D.na && (bv - D.na) % 3u == 0u) atomicAdd(D.act + (bv - D.na) / 3u, 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase)
+{
+    View V;
+    V.w = vbase;
+    V.na_v = D.view_atoms;
+    V.aux_base = ((D.view_atoms + 15u) >> 4) << 4;
+    V.auxlo = __ldg(D.cta_auxlo + blockIdx.x);
+    V.auxn = __ldg(D.cta_auxn + blockIdx.x);
+    return V;
+}
+
+__global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
+{
+    extern __shared__ unsigned long long smem_raw[];
+    Smem S;
+    S.bm = smem_raw;
+    S.red = S.bm + D.WW;
+    S.misc = reinterpret_cast<uint32_t *>(S.red + 32);
+    const View V = make_view(D, S.misc + 16);
+    __shared__ Ctl sC;
+    __shared__ Acc sA;
+
+    const bool cta0 = blockIdx.x == 0;
+    const bool leader = cta0 && threadIdx.x == 0;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long t_start = 0, t_phase = 0;
+    if (leader) { t_start = globaltimer_ns(); t_phase = t_start; }
+
+    if (threadIdx.x == 0) sC = D.ctl[0];
+    __syncthreads();
+    view_reload(D, V, 4u << (sC.round & 1u));
+    __syncthreads();
+
+    for (uint32_t k = 0;; k++) {
+        if (threadIdx.x == 0) {
+            sC = D.ctl[k & 1u];
+            sA = D.acc[(k + 3u) & 3u];
+        }
+        __syncthreads();
+        const Ctl C = sC;
+        const Acc A = sA;
+        if (C.op == OP_DONE) break;
+        Acc *acc = D.acc + (k & 3u);
+        Ctl N = C;
+        int kind = 0;   // 0 sweep, 1 analysis, 2 decision, 3 stability
+        const uint32_t tend = C.tb + A.nclaim;
+        const uint32_t fresh_cur = 4u << (C.round & 1u);
+        const uint32_t fresh_prev = 4u << ((C.round + 1u) & 1u);
+
+        switch (C.op) {
+        case OP_INIT: {
+            SweepCtx X{&D, V, fresh_cur, 1u, tend, acc, true, false, 0xFFFFFFFFu};
+            for (uint32_t i = gtid; i < D.n_units; i += nthreads) {
+                uint32_t id = D.units_base + i;
+                uint32_t l = __ldg(D.lits + id) & ~END_BIT;
+                uint32_t v = l >> 1;
+                uint32_t val = global_val(D, v, fresh_cur);
+                uint32_t own = (l & 1u) ? V_F : V_T;
+                if (val == 0u) {
+                    int r = claim_var(D.asg, v, (l & 1u) ? V_T : V_F, fresh_cur);
+                    if (r == 0) record_claim(X, v, id);
+                    else if (r == 2) report_conflict(X, id, 1u);
+                } else if (val == own) {
+                    report_conflict(X, id, 1u);
+                }
+            }
+            if (leader) {
+                N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = C.tc; N.clean = 0;
+            }
+            break;
+        }
+        case OP_ROUND: {
+            if (A.ckey != NO_KEY) {
+                kind = 1;
+                if (D.mode == MODE_PROPAGATE || C.cdl <= 1u) {
+                    if (leader) {
+                        N.op = OP_DONE;
+                        N.conflict = 1;
+                        N.status = C.n_models > 0 ? 10 : 20;
+                        atomicAdd(&D.stats->conflicts, 1ull);
+                    }
+                    break;
+                }
+                if (cta0) {
+                    uint32_t g = (uint32_t)(A.ckey & 0xFFFFFFFFull);
+                    analyze(D, S, g, C.cdl, C.lfill, true);
+                    if (leader) {
+                        atomicAdd(&D.stats->conflicts, 1ull);
+                        if (S.misc[0]) {
+                            N.op = OP_DONE;
+                            N.status = C.n_models > 0 ? 10 : 20;
+                        } else {
+                            uint32_t n = S.misc[2];
+                            if (C.lfill + n + 64u >= D.lits_cap || C.n_learned + 1u >= D.learned_ng_cap) {
+                                N.op = OP_DONE; N.err = -6; N.status = 0;
+                            } else {
+                                D.learned_ids[C.n_learned] = C.lfill;
+                                N.n_learned = C.n_learned + 1u;
+                                N.lfill = C.lfill + n;
+                                N.op = OP_BACKJUMP;
+                                N.target = S.misc[1];
+                                N.tb = tend;
+                                atomicAdd(&D.stats->learned, 1ull);
+                                atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
+                            }
+                        }
+                    }
+                }
+                break;
+            }
+            if (A.nclaim == 0u && C.clean) {
+                // fixpoint
+                if (D.mode == MODE_PROPAGATE) {
+                    if (leader) { N.op = OP_DONE; N.status = 0; }
+                    break;
+                }
+                if (tend >= D.nv) {
+                    kind = 3;
+                    if (leader) N.op = OP_STAB_INIT;
+                    break;
+                }
+                kind = 2;
+                decide(D, S, acc, gtid, nthreads);
+                if (leader) N.op = OP_APPLY;
+                break;
+            }
+            // make last round's claims visible: clear their fresh bit
+            // (grid-wide) and put them in this CTA's view
+            for (uint32_t i = C.tc + gtid; i < tend; i += nthreads) {
+                uint32_t v = __ldcg(D.trail + i);
+                atomicAnd(D.asg + (v >> 3), ~(fresh_prev << ((v & 7u) * 4u)));
+            }
+            if (tend - C.tc > 4096u) {
+                view_reload(D, V, fresh_cur);
+            } else {
+                for (uint32_t i = C.tc + threadIdx.x; i < tend; i += blockDim.x) {
+                    uint32_t v = __ldcg(D.trail + i);
+                    uint32_t val = nib(__ldcg(D.asg + (v >> 3)), v) & 3u;
+                    if (val == V_T || val == V_F) view_set(V, v, val);
+                }
+            }
+            __syncthreads();
+            SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, true, 0xFFFFFFFFu};
+            sweep(X, C.n_learned);
+            if (leader) {
+                N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1;
+                atomicAdd(&D.stats->rounds, 1ull);
+                atomicAdd(&D.stats->props, (unsigned long long)(tend - C.tc));
+                atomicAdd(&D.stats->checks, D.static_checks);
+            }
+            break;
+        }
+        case OP_APPLY: {
+            if (A.dkey == 0ull) {
+                // CompleteAssignment: falsify the unassigned atoms; their
+                // dependency bitmap is every decision level so far
+                kind = 2;
+                SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, false, 0xFFFFFFFFu};
+                const uint32_t nw = deps_words(D, C.cdl);
+                for (uint32_t p = gtid; p < D.na; p += nthreads) {
+                    if ((nib(__ldcg(D.asg + (p >> 3)), p) & 3u) != 0u) continue;
+                    if (claim_var(D.asg, p, V_F, fresh_cur) == 0) {
+                        record_claim(X, p, R_COMPLETE);
+                        if (C.cdl > 1u)
+                            for (uint32_t w = 0; w < nw; w++)
+                                D.deps[(size_t)p * D.WW + w] = all_levels_word(D, C.cdl, w);
+                    }
+                }
+                if (leader) {
+                    N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = tend; N.clean = 0;
+                    atomicAdd(&D.stats->completions, 1ull);
+                }
+                break;
+            }
+            const uint32_t j = 0xFFFFFFFFu - (uint32_t)(A.dkey & 0xFFFFFFFFull);
+            const uint32_t L = C.cdl + 1u;
+            const uint32_t bv = D.na + 3u * j;
+            if (leader) {
+                D.level_start[L] = tend;
+                D.dec_var[L] = bv;
+                D.trail[tend] = bv;
+                D.dl[bv] = (int32_t)L;
+                D.reason[bv] = R_DECISION;
+                uint32_t nw = deps_words(D, L), bit = level_bit(D, L);
+                for (uint32_t w = 0; w < nw; w++)
+                    D.deps[(size_t)bv * D.WW + w] = (w == (bit >> 6)) ? (1ull << (bit & 63u)) : 0ull;
+                __threadfence();
+                atomicOr(D.asg + (bv >> 3), V_T << ((bv & 7u) * 4u));
+            }
+            if (threadIdx.x == 0) view_set(V, bv, V_T);
+            __syncthreads();
+            SweepCtx X{&D, V, fresh_cur, L, tend + 1u, acc, true, true, bv};
+            sweep(X, C.n_learned);
+            if (leader) {
+                N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
+                N.clean = 0;
+                atomicAdd(&D.stats->decisions, 1ull);
+                atomicAdd(&D.stats->rounds, 1ull);
+                atomicAdd(&D.stats->checks, D.static_checks);
+                if ((unsigned long long)L > D.stats->max_level) D.stats->max_level = L;
+            }
+            break;
+        }
+        case OP_BACKJUMP: {
+            kind = 1;
+            const uint32_t newend = __ldcg(D.level_start + C.target + 1u);
+            for (uint32_t i = newend + gtid; i < tend; i += nthreads) {
+                uint32_t v = __ldcg(D.trail + i);
+                atomicAnd(D.asg + (v >> 3), ~(0xFu << ((v & 7u) * 4u)));
+                D.dl[v] = 0;
+            }
+            for (uint32_t i = newend + threadIdx.x; i < tend; i += blockDim.x)
+                view_clear(V, __ldcg(D.trail + i));
+            if (leader) {
+                N.op = OP_ROUND; N.cdl = C.target; N.tc = newend; N.tb = newend; N.clean = 0;
+            }
+            break;
+        }
+        case OP_STAB_INIT: {
+            kind = 3;
+            const uint32_t words = (D.na + 31u) >> 5;
+            for (uint32_t w = gtid; w < words; w += nthreads) D.lm[w] = 0u;
+            if (leader) { N.op = OP_STAB_ITER; N.stab_first = 1; N.tb = tend; }
+            break;
+        }
+        case OP_STAB_ITER: {
+            kind = 3;
+            if (!C.stab_first && A.flag == 0u) {
+                // least model reached: look for true atoms outside it
+                for (uint32_t p = gtid; p < D.na; p += nthreads) {
+                    bool inM = (nib(__ldcg(D.asg + (p >> 3)), p) & 3u) == V_T;
+                    bool inLM = (__ldcg(D.lm + (p >> 5)) >> (p & 31u)) & 1u;
+                    if (inM && !inLM) atomicMin(&acc->minU, p);
+                }
+                if (leader) N.op = OP_STAB_RESULT;
+                break;
+            }
+            // one pass of T over the reduct: rules whose negative body avoids
+            // M and whose positive body lies in the current set
+            for (uint32_t j = gtid; j < D.J; j += nthreads) {
+                uint32_t h = (uint32_t)__ldg(D.rule_head + j);
+                if ((__ldcg(D.lm + (h >> 5)) >> (h & 31u)) & 1u) continue;
+                bool ok = true;
+                for (uint32_t q = __ldg(D.rneg_off + j); ok && q < __ldg(D.rneg_off + j + 1); q++) {
+                    uint32_t a = __ldg(D.rneg + q);
+                    if ((nib(__ldcg(D.asg + (a >> 3)), a) & 3u) == V_T) ok = false;
+                }
+                for (uint32_t q = __ldg(D.rpos_off + j); ok && q < __ldg(D.rpos_off + j + 1); q++) {
+                    uint32_t a = __ldg(D.rpos + q);
+                    if (!((__ldcg(D.lm + (a >> 5)) >> (a & 31u)) & 1u)) ok = false;
+                }
+                if (ok) {
+                    atomicOr(D.lm + (h >> 5), 1u << (h & 31u));
+                    atomicOr(&acc->flag, 1u);
+                }
+            }
+            if (leader) { N.op = OP_STAB_ITER; N.stab_first = 0; }
+            break;
+        }
+        case OP_STAB_RESULT: {
+            kind = 3;
+            if (A.minU == 0xFFFFFFFFu) {
+                // answer set: record it, then block it with the decision literals
+                const long long row = C.n_models;
+                const uint32_t words = (D.na + 63u) >> 6;
+                if (row < D.models_cap) {
+                    for (uint32_t w = gtid; w < words; w += nthreads) {
+                        unsigned long long m = 0;
+                        for (uint32_t q = 0; q < 64u; q++) {
+                            uint32_t p = w * 64u + q;
+                            if (p < D.na && (nib(__ldcg(D.asg + (p >> 3)), p) & 3u) == V_T) m |= 1ull << q;
+                        }
+                        D.models[(size_t)row * words + w] = m;
+                    }
+                }
+                if (leader) {
+                    atomicAdd(&D.stats->models, 1ull);
+                    N.n_models = C.n_models + 1;
+                    if ((D.max_models > 0 && N.n_models >= D.max_models) || C.cdl <= 1u) {
+                        N.op = OP_DONE; N.status = 10;
+                    } else if (C.lfill + C.cdl + 64u >= D.lits_cap || C.n_learned + 1u >= D.learned_ng_cap) {
+                        N.op = OP_DONE; N.err = -6; N.status = 10;
+                    } else {
+                        uint32_t n = 0;
+                        for (uint32_t level = 2; level <= C.cdl; level++)
+                            D.lits[C.lfill + n++] = mk_lit(__ldcg(D.dec_var + level), false);
+                        D.lits[C.lfill + n - 1u] |= END_BIT;
+                        D.learned_ids[C.n_learned] = C.lfill;
+                        N.n_learned = C.n_learned + 1u;
+                        N.lfill = C.lfill + n;
+                        N.op = OP_BACKJUMP;
+                        N.target = C.cdl - 1u;
+                        atomicAdd(&D.stats->learned, 1ull);
+                        atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
+                    }
+                }
+                break;
+            }
+            // not an answer set: loop nogood {Tp} u {Fb_j : head(j) in U,
+            // body+(j) disjoint from U} for U = M \ LM(reduct), p = min U
+            const uint32_t p = A.minU;
+            for (uint32_t j = gtid; j < D.J; j += nthreads) {
+                uint32_t h = (uint32_t)__ldg(D.rule_head + j);
+                bool hU = ((nib(__ldcg(D.asg + (h >> 3)), h) & 3u) == V_T) && !((__ldcg(D.lm + (h >> 5)) >> (h & 31u)) & 1u);
+                if (!hU) continue;
+                bool ext = true;
+                for (uint32_t q = __ldg(D.rpos_off + j); ext && q < __ldg(D.rpos_off + j + 1); q++) {
+                    uint32_t a = __ldg(D.rpos + q);
+                    bool aU = ((nib(__ldcg(D.asg + (a >> 3)), a) & 3u) == V_T) && !((__ldcg(D.lm + (a >> 5)) >> (a & 31u)) & 1u);
+                    if (aU) ext = false;
+                }
+                if (ext) {
+                    uint32_t pos = C.lfill + 1u + atomicAdd(&acc->nlits, 1u);
+                    if (pos + 64u < D.lits_cap) D.lits[pos] = mk_lit(D.na + 3u * j, true);
+                }
+            }
+            if (leader) {
+                D.lits[C.lfill] = mk_lit(p, false);
+                N.op = OP_ANALYZE_ID;
+                N.conf_id = C.lfill;
+                atomicAdd(&D.stats->loops, 1ull);
+            }
+            break;
+        }
+        case OP_ANALYZE_ID: {
+            kind = 1;
+            const uint32_t len = 1u + A.nlits;
+            if (C.lfill + len + C.cdl + 64u >= D.lits_cap || C.n_learned + 2u >= D.learned_ng_cap) {
+                if (leader) { N.op = OP_DONE; N.err = -6; N.status = C.n_models > 0 ? 10 : 0; }
+                break;
+            }
+            if (cta0) {
+                if (leader) {
+                    D.lits[C.lfill + len - 1u] |= END_BIT;
+                    D.learned_ids[C.n_learned] = C.lfill;
+                    __threadfence();
+                }
+                __syncthreads();
+                const uint32_t lf = C.lfill + len;
+                analyze(D, S, C.conf_id, C.cdl, lf, false);
+                if (leader) {
+                    atomicAdd(&D.stats->conflicts, 1ull);
+                    atomicAdd(&D.stats->learned, 1ull);
+                    atomicAdd(&D.stats->learned_lits, (unsigned long long)len);
+                    if (S.misc[0]) {
+                        N.op = OP_DONE;
+                        N.status = C.n_models > 0 ? 10 : 20;
+                        N.n_learned = C.n_learned + 1u;
+                        N.lfill = lf;
+                    } else {
+                        uint32_t n = S.misc[2];
+                        D.learned_ids[C.n_learned + 1u] = lf;
+                        N.n_learned = C.n_learned + 2u;
+                        N.lfill = lf + n;
+                        N.op = OP_BACKJUMP;
+                        N.target = S.misc[1];
+                        atomicAdd(&D.stats->learned, 1ull);
+                        atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
+                    }
+                }
+            }
+            break;
+        }
+        default:
+            if (leader) { N.op = OP_DONE; N.err = -6; }
+            break;
+        }
+
+        if (leader) {
+            if (D.mode == MODE_SOLVE && N.op != OP_DONE) {
+                unsigned long long now = globaltimer_ns();
+                bool over_time = D.time_budget_ns > 0 && (long long)(now - t_start) > D.time_budget_ns;
+                bool over_conf = D.conflict_budget > 0 && (long long)D.stats->conflicts >= D.conflict_budget;
+                if (over_time || over_conf) { N.op = OP_DONE; N.status = N.n_models > 0 ? 10 : 0; }
+            }
+            D.ctl[(k + 1u) & 1u] = N;
+            Acc z;
+            z.ckey = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0;
+            D.acc[(k + 1u) & 3u] = z;
+            // fold long-nogood checks of the previous phase into the stats
+            if (A.checks) atomicAdd(&D.stats->checks, A.checks);
+            unsigned long long now = globaltimer_ns();
+            unsigned long long dt = now - t_phase;
+            t_phase = now;
+            unsigned long long *bucket = kind == 0 ? &D.stats->ns_sweep : kind == 1 ? &D.stats->ns_analysis
+                                       : kind == 2 ? &D.stats->ns_decision : &D.stats->ns_stab;
+            *bucket += dt;
+            D.stats->phases += 1;
+            __threadfence();
+        }
+        if (!grid_sync(D.bar, gridDim.x)) break;
+    }
+    if (leader) {
+        const Ctl F = sC;
+        D.stats->pad = F.tc;
+        D.stats->ns_total = globaltimer_ns() - t_start;
+        int err = F.err;
+        if (__ldcg(&D.bar->err)) err = -6;
+        D.result[0] = F.status;
+        D.result[1] = F.n_models;
+        D.result[2] = err;
+        D.result[3] = F.conflict;
+    }
+}
+
+// One sweep over the static store without claiming (timing the sweep kernel
+// in isolation): counts unit nogoods in acc->flag, conflicts in acc->ckey.
+// Same partition, views and classification as the solver's sweep.
+__global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc)
+{
+    extern __shared__ unsigned long long smem_raw[];
+    uint32_t *vbase = reinterpret_cast<uint32_t *>(smem_raw + D.WW + 32) + 16;
+    const View V = make_view(D, vbase);
+    view_reload(D, V, 0u);
+    __syncthreads();
+    SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu};
+    sweep(X, 0u);
+}
+
+}  // namespace aspgpu
+
+// ------------------------------------------------------------ launchers
+
+namespace aspgpu {
+
+cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block, smem);
+}
+
+cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st)
+{
+    Dev copy = D;
+    void *args[] = {(void *)&copy};
+    return cudaLaunchCooperativeKernel((void *)solve_kernel, dim3(grid), dim3(block), args, smem, st);
+}
+
+cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st)
+{
+    sweep_kernel<<<grid, block, smem, st>>>(D, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace aspgpu

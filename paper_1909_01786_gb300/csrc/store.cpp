@@ -1,0 +1,179 @@
+// Completion nogoods of a ground normal program, packed for the device
+// (Section 2 for the nogoods; Section 4 for the store sorted by length).
+//
+// Rules with a head are renumbered in order of their head atom, so rules(p)
+// is a contiguous range.  Nogoods are generated group by group: for each atom
+// p, the nogoods of each rule of p followed by p's own nogood
+// {Tp} u {Fb_r : r in rules(p)}; then one group per constraint.  Each nogood
+// goes to the bucket of its exact length (2..BUCKET_MAX; Section 4 uses one
+// kernel per length class), keeping group order inside a bucket, so the
+// nogoods of a range of groups refer to a contiguous range of auxiliary
+// variables b_r, t_r, n_r, which a CTA keeps in shared memory.  Unit nogoods
+// go to a separate list that InitialPropagation applies once (Algorithm 1);
+// longer nogoods go to a CSR region.
+#include "store.h"
+
+#include <algorithm>
+#include <cstring>
+
+#include "aspgpu.h"
+
+namespace aspgpu {
+
+namespace {
+
+struct Packer {
+    HostStore &S;
+    uint32_t group = 0;
+
+    explicit Packer(HostStore &s) : S(s) {}
+
+    void add(const uint32_t *l, int64_t len) {
+        S.n_nogoods++;
+        S.n_literals += len;
+        if (len == 0) { S.has_empty_nogood = true; return; }
+        if (len == 1) { S.units.push_back(l[0]); return; }
+        S.group_lits[group] += (uint64_t)len;
+        if (len > BUCKET_MAX) {
+            S.long_rel.push_back((uint32_t)S.long_lits.size());
+            for (int64_t i = 0; i < len; i++) S.long_lits.push_back(l[i] | (i == len - 1 ? END_BIT : 0u));
+            return;
+        }
+        S.bucket_rows[len].insert(S.bucket_rows[len].end(), l, l + len);
+        S.bucket_group[len].push_back(group);
+    }
+};
+
+}  // namespace
+
+int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
+                const int64_t *pos_off, const int32_t *pos,
+                const int64_t *neg_off, const int32_t *neg,
+                HostStore &S, std::string &err)
+{
+    if (n_atoms < 0 || n_rules < 0) { err = "negative size"; return ASP_E_ARG; }
+    if (n_rules > 0 && (!head || !pos_off || !neg_off)) { err = "null rule array"; return ASP_E_ARG; }
+    if (n_rules > 0 && (pos_off[0] != 0 || neg_off[0] != 0)) { err = "offsets must start at 0"; return ASP_E_ARG; }
+    int64_t n_headed = 0;
+    for (int32_t r = 0; r < n_rules; r++) {
+        if (pos_off[r + 1] < pos_off[r] || neg_off[r + 1] < neg_off[r]) { err = "offsets not monotone"; return ASP_E_ARG; }
+        if (head[r] < -1 || head[r] >= n_atoms) { err = "head atom out of range"; return ASP_E_RANGE; }
+        n_headed += head[r] >= 0;
+    }
+    if ((pos_off && pos_off[n_rules] > 0 && !pos) || (neg_off && neg_off[n_rules] > 0 && !neg)) {
+        err = "null body array"; return ASP_E_ARG;
+    }
+    for (int64_t k = 0; n_rules > 0 && k < pos_off[n_rules]; k++)
+        if (pos[k] < 0 || pos[k] >= n_atoms) { err = "body atom out of range"; return ASP_E_RANGE; }
+    for (int64_t k = 0; n_rules > 0 && k < neg_off[n_rules]; k++)
+        if (neg[k] < 0 || neg[k] >= n_atoms) { err = "body atom out of range"; return ASP_E_RANGE; }
+    int64_t nv = (int64_t)n_atoms + 3 * n_headed;
+    if (nv > MAX_VARS) { err = "too many variables (atoms + 3 x rules >= 2^30)"; return ASP_E_RANGE; }
+
+    S = HostStore();
+    S.n_atoms = n_atoms;
+    S.n_rules = n_rules;
+    S.n_headed = (int32_t)n_headed;
+    S.n_vars = nv;
+    const uint32_t J = (uint32_t)n_headed, A = (uint32_t)n_atoms;
+    auto bvar = [&](uint32_t j) { return A + 3 * j; };
+    auto tvar = [&](uint32_t j) { return A + 3 * j + 1; };
+    auto nvar = [&](uint32_t j) { return A + 3 * j + 2; };
+
+    // headed rules sorted by head atom (ties in input order), bodies
+    // deduplicated: rules(p) is then a contiguous index range
+    std::vector<int32_t> order;
+    order.reserve(J);
+    for (int32_t r = 0; r < n_rules; r++) if (head[r] >= 0) order.push_back(r);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return head[a] < head[b]; });
+    S.rule_index = order;
+    S.rule_head.reserve(J);
+    S.rpos_off.push_back(0);
+    S.rneg_off.push_back(0);
+    std::vector<uint32_t> mark((size_t)n_atoms + 1, 0);
+    uint32_t stamp = 0;
+    for (int32_t r : order) {
+        S.rule_head.push_back(head[r]);
+        ++stamp;
+        for (int64_t k = pos_off[r]; k < pos_off[r + 1]; k++)
+            if (mark[pos[k]] != stamp) { mark[pos[k]] = stamp; S.rpos.push_back((uint32_t)pos[k]); }
+        S.rpos_off.push_back((uint32_t)S.rpos.size());
+        ++stamp;
+        for (int64_t k = neg_off[r]; k < neg_off[r + 1]; k++)
+            if (mark[neg[k]] != stamp) { mark[neg[k]] = stamp; S.rneg.push_back((uint32_t)neg[k]); }
+        S.rneg_off.push_back((uint32_t)S.rneg.size());
+    }
+
+    // p -> OR_{r in rules(p)} b_r needs rules(p): contiguous after sorting
+    std::vector<uint32_t> first((size_t)n_atoms + 1, 0);
+    for (uint32_t j = 0; j < J; j++) first[S.rule_head[j] + 1]++;
+    for (int32_t p = 0; p < n_atoms; p++) first[p + 1] += first[p];
+
+    int64_t n_constraints = (int64_t)n_rules - (int64_t)n_headed;
+    S.n_groups = (int32_t)(n_atoms + n_constraints);
+    S.group_lits.assign((size_t)S.n_groups + 1, 0);
+    Packer pk(S);
+    std::vector<uint32_t> buf;
+    auto rule_nogoods = [&](uint32_t j) {
+        uint32_t b = bvar(j), t = tvar(j), n = nvar(j);
+        uint32_t x[3];
+        // b_r <-> t_r & n_r : {Fb,Tt,Tn} {Tb,Ft} {Tb,Fn}
+        x[0] = mk_lit(b, true); x[1] = mk_lit(t, false); x[2] = mk_lit(n, false); pk.add(x, 3);
+        x[0] = mk_lit(b, false); x[1] = mk_lit(t, true); pk.add(x, 2);
+        x[0] = mk_lit(b, false); x[1] = mk_lit(n, true); pk.add(x, 2);
+        // t_r <-> body+ : {Tt,Fp} per p, {Ft} u {Tp}
+        buf.assign(1, mk_lit(t, true));
+        for (uint32_t k = S.rpos_off[j]; k < S.rpos_off[j + 1]; k++) {
+            x[0] = mk_lit(t, false); x[1] = mk_lit(S.rpos[k], true); pk.add(x, 2);
+            buf.push_back(mk_lit(S.rpos[k], false));
+        }
+        pk.add(buf.data(), (int64_t)buf.size());
+        // n_r <-> not body- : {Tn,Tq} per q, {Fn} u {Fq}
+        buf.assign(1, mk_lit(n, true));
+        for (uint32_t k = S.rneg_off[j]; k < S.rneg_off[j + 1]; k++) {
+            x[0] = mk_lit(n, false); x[1] = mk_lit(S.rneg[k], false); pk.add(x, 2);
+            buf.push_back(mk_lit(S.rneg[k], true));
+        }
+        pk.add(buf.data(), (int64_t)buf.size());
+        // head <- b_r : {Fhead, Tb}
+        x[0] = mk_lit((uint32_t)S.rule_head[j], true); x[1] = mk_lit(b, false); pk.add(x, 2);
+    };
+    for (int32_t p = 0; p < n_atoms; p++) {
+        pk.group = (uint32_t)p;
+        for (uint32_t j = first[p]; j < first[p + 1]; j++) rule_nogoods(j);
+        // p -> OR_{r in rules(p)} b_r : {Tp} u {Fb_r}
+        buf.assign(1, mk_lit((uint32_t)p, false));
+        for (uint32_t j = first[p]; j < first[p + 1]; j++) buf.push_back(mk_lit(bvar(j), true));
+        pk.add(buf.data(), (int64_t)buf.size());
+    }
+    // constraints {Tp1..Tpm, Fpm+1..Fpn} (repeated literals once)
+    uint32_t cgroup = (uint32_t)n_atoms;
+    for (int32_t r = 0; r < n_rules; r++) {
+        if (head[r] >= 0) continue;
+        pk.group = cgroup++;
+        buf.clear();
+        for (int64_t k = pos_off[r]; k < pos_off[r + 1]; k++) buf.push_back(mk_lit((uint32_t)pos[k], false));
+        for (int64_t k = neg_off[r]; k < neg_off[r + 1]; k++) buf.push_back(mk_lit((uint32_t)neg[k], true));
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+        pk.add(buf.data(), (int64_t)buf.size());
+    }
+    // static decision score: occurrences of the head atom in the nogoods
+    std::vector<uint32_t> occ((size_t)n_atoms + 1, 0);
+    auto count = [&](uint32_t w) {
+        uint32_t v = (w & ~END_BIT) >> 1;
+        if (v < A) occ[v]++;
+    };
+    for (int L = 2; L <= BUCKET_MAX; L++) for (uint32_t w : S.bucket_rows[L]) count(w);
+    for (uint32_t w : S.long_lits) count(w);
+    for (uint32_t u : S.units) count(u);
+    S.score.resize(J);
+    for (uint32_t j = 0; j < J; j++) S.score[j] = occ[S.rule_head[j]];
+
+    for (int L = 2; L <= BUCKET_MAX; L++)
+        if (S.bucket_group[L].size() >= (1u << 27)) { err = "too many nogoods of one length (>= 2^27)"; return ASP_E_RANGE; }
+    if ((uint64_t)S.n_literals >= 0x7FFF0000ull) { err = "nogood store exceeds 2^31 literals"; return ASP_E_RANGE; }
+    return ASP_OK;
+}
+
+}  // namespace aspgpu
