@@ -161,6 +161,35 @@ int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *leve
  * sign 1 = F; returns the length, writes at most cap literals. */
 int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap);
 
+/* ---- allocation-free propagation ---------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory where they need propagation -- code
+ * running while a stream is being captured into a CUDA graph, real-time
+ * loops that must not enter the allocator, or processes whose device memory
+ * is reserved up front.  It computes the same closure as
+ * asp_debug_propagate (unit propagation of a root-level partial assignment
+ * to fixpoint over the program's nogoods) but keeps all of its working
+ * memory in one static device array inside the library: at most 2^20
+ * solver variables (512 KB of 4-bit codes plus 256 B of counters), held by
+ * every GPU that loads the library until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   p          a program loaded earlier with asp_load_ground (read only)
+ *   d_partial  device int8[n_vars]: 1 true, -1 false, 0 unassigned
+ *   d_closure  device int8[n_vars] output: 1 / -1 / 0 (2 marks a variable
+ *              both values were claimed for, only after a conflict)
+ *   d_conflict device int32 output: 1 if a nogood became violated,
+ *              -1 on a device-side barrier timeout, else 0
+ * The work is enqueued on the program's stream; the call returns without
+ * synchronising.  Returns ASP_E_CAPACITY if the program has more than 2^20
+ * variables, ASP_E_ARG on null pointers, ASP_E_CUDA on a CUDA error.
+ * The first call on a device looks up the device address of the static
+ * array (cudaGetSymbolAddress) and the kernel's occupancy; make that first
+ * call before any stream capture.  Every call shares the one array: calls
+ * that overlap on the GPU (other streams, other host threads) race on it and
+ * give wrong results.  Each call clears the counters it needs at zero. */
+int asp_propagate_noalloc(const asp_prog *p, const int8_t *d_partial, int8_t *d_closure,
+                          int32_t *d_conflict);
+
 #ifdef __cplusplus
 }
 #endif

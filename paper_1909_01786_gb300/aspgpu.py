@@ -48,7 +48,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep_once",
-           "asp_debug_state", "asp_debug_nogood"]
+           "asp_debug_state", "asp_debug_nogood", "asp_propagate_noalloc"]
 
 
 def library_path() -> str:
@@ -92,6 +92,8 @@ def lib(build_if_missing: bool = True):
         L.asp_debug_state.restype = C.c_int
         L.asp_debug_nogood.argtypes = [vp, C.c_uint32, vp, i64]
         L.asp_debug_nogood.restype = i64
+        L.asp_propagate_noalloc.argtypes = [vp, vp, vp, vp]
+        L.asp_propagate_noalloc.restype = C.c_int
         _lib = L
         return L
 
@@ -202,6 +204,11 @@ class Program:
         conf = C.c_int32()
         _check(lib().asp_debug_propagate(self.handle, p.ctypes.data, out.ctypes.data, C.byref(conf)))
         return bool(conf.value), out
+
+    def propagate_noalloc(self, d_partial: int, d_closure: int, d_conflict: int) -> int:
+        """asp_propagate_noalloc on device buffers (int8 / int8 / int32
+        pointers); enqueued on the program's stream.  Returns the ABI code."""
+        return lib().asp_propagate_noalloc(self.handle, d_partial, d_closure, d_conflict)
 
     def sweep_once(self):
         _check(lib().asp_sweep_once(self.handle))

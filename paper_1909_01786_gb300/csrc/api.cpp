@@ -27,6 +27,10 @@ static int fail(int code, const std::string &msg)
     return code;
 }
 
+namespace aspgpu {
+int internal_fail(int code, const char *msg) { return fail(code, msg); }
+}  // namespace aspgpu
+
 static int cuda_fail(cudaError_t e, const char *what)
 {
     return fail(ASP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -50,6 +54,13 @@ struct asp_prog {
     int64_t d_models_rows = 0;
     Acc *d_sweep_acc = nullptr;
 };
+
+namespace aspgpu {
+// for entry points defined in other translation units
+const Dev *internal_dev(const asp_prog *p) { return &p->D; }
+cudaStream_t internal_stream(const asp_prog *p) { return p->stream; }
+int internal_fail(int code, const char *msg);
+}  // namespace aspgpu
 
 static void *dalloc(asp_prog *p, size_t bytes)
 {
