@@ -15,6 +15,9 @@ namespace aspgpu {
 cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t batch_configure(size_t smem, int *blocks_per_sm);
+cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
+                         size_t smem, cudaStream_t st);
 }  // namespace aspgpu
 
 using namespace aspgpu;
@@ -46,6 +49,8 @@ struct asp_prog {
     Dev D{};
     int grid = 1, block = 1024;
     size_t smem = 0;
+    Dev D1{};           // the same program as one CTA solves it in a batch
+    size_t smem1 = 0;
     int64_t n_nogoods = 0, n_literals = 0, n_units = 0, n_long = 0, store_bytes = 0;
     bool empty_nogood = false;
     // internal buffers for the blocking entry points
@@ -179,6 +184,37 @@ static int plan_grid(asp_prog *p, const HostStore &H)
     return ASP_OK;
 }
 
+// Single-CTA layout of the program for batched solving: the whole store is
+// the CTA's range, and the view holds every atom and auxiliary variable if
+// they fit in the per-CTA shared-memory budget of the batch kernel.
+constexpr size_t BATCH_SMEM_BUDGET = 72 * 1024 - 1024;
+
+static int plan_batch(asp_prog *p, const HostStore &H)
+{
+    Dev D1 = p->D;
+    std::vector<uint32_t> boff(32, 0), alo(1), an(1);
+    for (int L = 2; L <= BUCKET_MAX; L++) boff[L * 2 + 1] = (uint32_t)H.bucket_group[L].size();
+    alo[0] = D1.na;
+    an[0] = 3 * D1.J;
+    const size_t base = 8ull * D1.WW + 8ull * 32 + 4ull * 16;
+    size_t aw = (D1.na + 15u) / 16u, xw = (an[0] + 15u) / 16u;
+    D1.view_atoms = D1.na;
+    if (base + 4 * (aw + xw) > BATCH_SMEM_BUDGET) {
+        D1.view_atoms = 0;
+        aw = 0;
+        if (base + 4 * xw > BATCH_SMEM_BUDGET) { an[0] = 0; xw = 0; }
+    }
+    D1.view_words = (uint32_t)(aw + xw);
+    D1.G = 1;
+    int rc = ASP_OK;
+    D1.cta_boff = upload(p, boff, rc);
+    if (rc == ASP_OK) D1.cta_auxlo = upload(p, alo, rc);
+    if (rc == ASP_OK) D1.cta_auxn = upload(p, an, rc);
+    p->D1 = D1;
+    p->smem1 = base + 4 * D1.view_words;
+    return rc;
+}
+
 extern "C" {
 
 void asp_default_options(asp_options *opt)
@@ -298,6 +334,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     p->d_result = (long long *)alloc(sizeof(long long) * 4);
     p->d_sweep_acc = (Acc *)alloc(sizeof(Acc));
     if (rc == ASP_OK) rc = plan_grid(p, H);
+    if (rc == ASP_OK) rc = plan_batch(p, H);
     if (rc == ASP_OK) {
         cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(e, "load");
@@ -576,14 +613,93 @@ int asp_solve_batch(int32_t n, asp_prog *const *progs, int64_t max_models_each,
                     int32_t *statuses, int64_t *n_models, uint64_t *const *models,
                     const int64_t *models_cap)
 {
-    // sequential fallback over the single-program device loop
-    if (n < 0 || (n > 0 && (!progs || !statuses || !n_models))) return fail(ASP_E_ARG, "bad argument");
+    g_err.clear();
+    if (n < 0 || max_models_each < 0 || (n > 0 && (!progs || !statuses || !n_models))) return fail(ASP_E_ARG, "bad argument");
+    if (n == 0) return ASP_OK;
     for (int32_t i = 0; i < n; i++) {
-        int64_t cap = models_cap ? models_cap[i] : 0;
-        uint64_t *m = models ? models[i] : nullptr;
-        int rc = asp_solve(progs[i], max_models_each, m, cap, &n_models[i], &statuses[i]);
-        if (rc != ASP_OK && rc != ASP_E_CAPACITY) return rc;
+        if (!progs[i]) return fail(ASP_E_ARG, "null program");
+        if (progs[i]->stream != progs[0]->stream) return fail(ASP_E_ARG, "programs loaded on different streams");
+        if (models_cap && models_cap[i] > 0 && (!models || !models[i])) return fail(ASP_E_ARG, "null model buffer");
     }
+    asp_prog *p0 = progs[0];
+    cudaStream_t st = p0->stream;
+    // per-program descriptors, largest store first in the queue
+    std::vector<Dev> devs(n);
+    std::vector<uint32_t> order(n);
+    size_t smem = 0;
+    for (int32_t i = 0; i < n; i++) {
+        asp_prog *p = progs[i];
+        const int64_t words = std::max<int64_t>(((int64_t)p->D.na + 63) / 64, 1);
+        const int64_t cap = models_cap ? models_cap[i] : 0;
+        const int64_t rows = std::max<int64_t>(cap, 1);
+        if (rows > p->d_models_rows) {
+            void *q = dalloc(p, (size_t)(rows * words) * 8);
+            if (!q) return fail(ASP_E_OOM, "device allocation failed (models)");
+            p->d_models = (unsigned long long *)q;
+            p->d_models_rows = rows;
+        }
+        Dev d = p->D1;
+        d.mode = MODE_SOLVE;
+        d.max_models = max_models_each;
+        d.models_cap = cap;
+        d.models = p->d_models;
+        d.result = p->d_result;
+        d.conflict_budget = p->opt.conflict_budget;
+        d.time_budget_ns = p->opt.time_budget_ms > 0 ? p->opt.time_budget_ms * 1000000ll : 0;
+        devs[i] = d;
+        order[i] = (uint32_t)i;
+        smem = std::max(smem, p->smem1);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return progs[a]->n_literals > progs[b]->n_literals; });
+    // per-call device scratch: descriptors, queue order, queue counter
+    const size_t bytes = sizeof(Dev) * (size_t)n + 4 * (size_t)n + 64;
+    void *scratch = nullptr;
+    if (p0->opt.dev_alloc) scratch = p0->opt.dev_alloc(bytes, p0->opt.alloc_ctx);
+    else if (cudaMalloc(&scratch, bytes) != cudaSuccess) { cudaGetLastError(); scratch = nullptr; }
+    if (!scratch) return fail(ASP_E_OOM, "device allocation failed (batch descriptors)");
+    auto release = [&]() {
+        if (p0->opt.dev_free) p0->opt.dev_free(scratch, bytes, p0->opt.alloc_ctx);
+        else cudaFree(scratch);
+    };
+    Dev *d_devs = (Dev *)scratch;
+    uint32_t *d_order = (uint32_t *)((char *)scratch + sizeof(Dev) * (size_t)n);
+    unsigned int *d_queue = (unsigned int *)((char *)d_order + 4 * (size_t)n);
+    int rc = ASP_OK;
+    int per_sm = 0;
+    cudaError_t e = cudaMemcpyAsync(d_devs, devs.data(), sizeof(Dev) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, 64, st);
+    if (e == cudaSuccess) e = batch_configure(smem, &per_sm);
+    if (e == cudaSuccess && per_sm < 1) { rc = fail(ASP_E_CUDA, "batch kernel cannot be resident"); }
+    if (e == cudaSuccess && rc == ASP_OK) {
+        int grid = (int)std::min<int64_t>((int64_t)p0->n_sms * per_sm, n);
+        e = launch_batch(d_devs, d_order, (uint32_t)n, d_queue, grid, smem, st);
+    }
+    if (e == cudaSuccess && rc == ASP_OK) e = st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize();
+    if (e != cudaSuccess && rc == ASP_OK) rc = cuda_fail(e, "batch solve");
+    bool device_error = false, capacity = false;
+    for (int32_t i = 0; i < n && rc == ASP_OK; i++) {
+        asp_prog *p = progs[i];
+        long long res[4];
+        e = cudaMemcpy(res, p->d_result, sizeof(res), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "batch result"); break; }
+        statuses[i] = (int32_t)res[0];
+        n_models[i] = res[1];
+        device_error |= res[2] != 0;
+        const int64_t cap = models_cap ? models_cap[i] : 0;
+        const int64_t words = ((int64_t)p->D.na + 63) / 64;
+        const int64_t copy = std::min<int64_t>(res[1], cap);
+        capacity |= res[1] > cap && cap > 0;
+        if (copy > 0 && words > 0) {
+            e = cudaMemcpy(models[i], p->d_models, (size_t)(copy * words) * 8, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "batch models"); break; }
+        }
+    }
+    release();
+    if (rc != ASP_OK) return rc;
+    if (device_error) return fail(ASP_E_DEVICE, "device-side error in some program (learned store full)");
+    if (capacity) return fail(ASP_E_CAPACITY, "more answer sets than model buffer rows for some program");
     return ASP_OK;
 }
 

@@ -238,6 +238,8 @@ struct SweepCtx {
     bool use_view;
     uint32_t dec_v;        // decision variable set in this phase (its level
                            // and bitmap are known here before they reach memory)
+    uint32_t cta;          // this CTA's part of the static partition
+    uint32_t gw, nw;       // warp index and warp count of the solving group
 };
 
 __device__ __forceinline__ void report_conflict(const SweepCtx &X, uint32_t id, uint32_t len)
@@ -471,8 +473,8 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
     const uint32_t G1 = D.G + 1u;
 #pragma unroll 1
     for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
-        const uint32_t b0 = __ldg(D.cta_boff + L * G1 + blockIdx.x);
-        const uint32_t b1 = __ldg(D.cta_boff + L * G1 + blockIdx.x + 1u);
+        const uint32_t b0 = __ldg(D.cta_boff + L * G1 + X.cta);
+        const uint32_t b1 = __ldg(D.cta_boff + L * G1 + X.cta + 1u);
         if (b1 <= b0) continue;
         switch (L) {
         case 2: run_bucket<2, 4>(X, b0, b1); break;
@@ -493,9 +495,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
     }
     unsigned long long checks = 0;
     const uint32_t nl = D.n_long + n_learned;
-    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t i = gwarp; i < nl; i += nwarps) {
+    for (uint32_t i = X.gw; i < nl; i += X.nw) {
         uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
         classify_long(X, id, checks);
     }
@@ -674,44 +674,72 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
     __syncthreads();
 }
 
-__device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase)
+__device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase, uint32_t cta)
 {
     View V;
     V.w = vbase;
     V.na_v = D.view_atoms;
     V.aux_base = ((D.view_atoms + 15u) >> 4) << 4;
-    V.auxlo = __ldg(D.cta_auxlo + blockIdx.x);
-    V.auxn = __ldg(D.cta_auxn + blockIdx.x);
+    V.auxlo = __ldg(D.cta_auxlo + cta);
+    V.auxn = __ldg(D.cta_auxn + cta);
     return V;
 }
 
-__global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
+// Copy of a control struct read through L2 (other threads update it with
+// plain stores and atomics).
+template <class T>
+__device__ __forceinline__ void ldcg_copy(T *dst, const T *src)
 {
-    extern __shared__ unsigned long long smem_raw[];
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+#pragma unroll
+    for (uint32_t i = 0; i < sizeof(T) / 4u; i++) d[i] = __ldcg(s + i);
+}
+
+__device__ __forceinline__ Smem make_smem(const Dev &D, unsigned long long *raw)
+{
     Smem S;
-    S.bm = smem_raw;
+    S.bm = raw;
     S.red = S.bm + D.WW;
     S.misc = reinterpret_cast<uint32_t *>(S.red + 32);
-    const View V = make_view(D, S.misc + 16);
+    return S;
+}
+
+// Phase barrier of the solving group: the whole grid (one program on every
+// SM) or one CTA (one program of a batch).
+template <bool BATCH>
+__device__ __forceinline__ bool group_sync(const Dev &D)
+{
+    if (BATCH) {
+        __syncthreads();
+        return true;
+    }
+    return grid_sync(D.bar, gridDim.x);
+}
+
+// Algorithm 1 on the device.  rank/size: thread index and thread count of
+// the solving group; cta: this CTA's part of the program's static partition;
+// cta0/leader: the CTA and thread that run conflict analysis and write the
+// next control block.
+template <bool BATCH>
+__device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const View &V, uint32_t rank,
+                                            uint32_t size, bool cta0, bool leader, uint32_t cta)
+{
     __shared__ Ctl sC;
     __shared__ Acc sA;
-
-    const bool cta0 = blockIdx.x == 0;
-    const bool leader = cta0 && threadIdx.x == 0;
-    const uint32_t nthreads = gridDim.x * blockDim.x;
-    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gtid = rank, nthreads = size;
     unsigned long long t_start = 0, t_phase = 0;
     if (leader) { t_start = globaltimer_ns(); t_phase = t_start; }
 
-    if (threadIdx.x == 0) sC = D.ctl[0];
+    if (threadIdx.x == 0) ldcg_copy(&sC, D.ctl);
     __syncthreads();
     view_reload(D, V, 4u << (sC.round & 1u));
     __syncthreads();
 
     for (uint32_t k = 0;; k++) {
         if (threadIdx.x == 0) {
-            sC = D.ctl[k & 1u];
-            sA = D.acc[(k + 3u) & 3u];
+            ldcg_copy(&sC, D.ctl + (k & 1u));
+            ldcg_copy(&sA, D.acc + ((k + 3u) & 3u));
         }
         __syncthreads();
         const Ctl C = sC;
@@ -726,7 +754,7 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
 
         switch (C.op) {
         case OP_INIT: {
-            SweepCtx X{&D, V, fresh_cur, 1u, tend, acc, true, false, 0xFFFFFFFFu};
+            SweepCtx X{&D, V, fresh_cur, 1u, tend, acc, true, false, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
             for (uint32_t i = gtid; i < D.n_units; i += nthreads) {
                 uint32_t id = D.units_base + i;
                 uint32_t l = __ldg(D.lits + id) & ~END_BIT;
@@ -817,7 +845,7 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
                 }
             }
             __syncthreads();
-            SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, true, 0xFFFFFFFFu};
+            SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, true, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
             sweep(X, C.n_learned);
             if (leader) {
                 N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1;
@@ -832,7 +860,7 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
                 // CompleteAssignment: falsify the unassigned atoms; their
                 // dependency bitmap is every decision level so far
                 kind = 2;
-                SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, false, 0xFFFFFFFFu};
+                SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, false, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
                 const uint32_t nw = deps_words(D, C.cdl);
                 for (uint32_t p = gtid; p < D.na; p += nthreads) {
                     if ((nib(__ldcg(D.asg + (p >> 3)), p) & 3u) != 0u) continue;
@@ -866,7 +894,7 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
             }
             if (threadIdx.x == 0) view_set(V, bv, V_T);
             __syncthreads();
-            SweepCtx X{&D, V, fresh_cur, L, tend + 1u, acc, true, true, bv};
+            SweepCtx X{&D, V, fresh_cur, L, tend + 1u, acc, true, true, bv, cta, rank >> 5, size >> 5};
             sweep(X, C.n_learned);
             if (leader) {
                 N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
@@ -1047,7 +1075,7 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
             if (D.mode == MODE_SOLVE && N.op != OP_DONE) {
                 unsigned long long now = globaltimer_ns();
                 bool over_time = D.time_budget_ns > 0 && (long long)(now - t_start) > D.time_budget_ns;
-                bool over_conf = D.conflict_budget > 0 && (long long)D.stats->conflicts >= D.conflict_budget;
+                bool over_conf = D.conflict_budget > 0 && (long long)__ldcg(&D.stats->conflicts) >= D.conflict_budget;
                 if (over_time || over_conf) { N.op = OP_DONE; N.status = N.n_models > 0 ? 10 : 0; }
             }
             D.ctl[(k + 1u) & 1u] = N;
@@ -1065,7 +1093,7 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
             D.stats->phases += 1;
             __threadfence();
         }
-        if (!grid_sync(D.bar, gridDim.x)) break;
+        if (!group_sync<BATCH>(D)) break;
     }
     if (leader) {
         const Ctl F = sC;
@@ -1080,6 +1108,60 @@ __global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
     }
 }
 
+__global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
+{
+    extern __shared__ unsigned long long smem_raw[];
+    const Smem S = make_smem(D, smem_raw);
+    const View V = make_view(D, S.misc + 16, blockIdx.x);
+    solver_loop<false>(D, S, V, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, blockIdx.x == 0,
+                       blockIdx.x == 0 && threadIdx.x == 0, blockIdx.x);
+}
+
+// Batched solving: each CTA takes programs from a queue (the host orders it
+// largest first) and solves each alone, with the whole program's assignment
+// view in its shared memory and __syncthreads as the phase barrier.
+__global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
+                                                       unsigned int *queue)
+{
+    extern __shared__ unsigned long long smem_raw[];
+    __shared__ Dev sD;
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t i = atomicAdd(queue, 1u);
+            s_item = i < n ? __ldg(order + i) : 0xFFFFFFFFu;
+            if (s_item != 0xFFFFFFFFu) sD = devs[s_item];
+        }
+        __syncthreads();
+        if (s_item == 0xFFFFFFFFu) break;
+        const Dev &D = sD;
+        // reset this program's search state
+        for (uint32_t w = threadIdx.x; w <= D.asg_words; w += blockDim.x) D.asg[w] = 0u;
+        for (uint32_t v = threadIdx.x; v < D.nv; v += blockDim.x) D.dl[v] = 0;
+        for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) D.act[j] = 0u;
+        if (threadIdx.x == 0) {
+            Ctl c;
+            memset(&c, 0, sizeof(c));
+            c.op = OP_INIT;
+            c.cdl = 1;
+            c.lfill = D.lits_static;
+            D.ctl[0] = c;
+            memset(&c, 0, sizeof(c));
+            D.ctl[1] = c;
+            Acc a;
+            a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+            for (int i = 0; i < 4; i++) D.acc[i] = a;
+            memset(D.stats, 0, sizeof(DevStats));
+            memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check
+        }
+        __syncthreads();
+        const Smem S = make_smem(D, smem_raw);
+        const View V = make_view(D, S.misc + 16, 0);
+        solver_loop<true>(D, S, V, threadIdx.x, blockDim.x, true, threadIdx.x == 0, 0);
+        __syncthreads();
+    }
+}
+
 // One sweep over the static store without claiming (timing the sweep kernel
 // in isolation): counts unit nogoods in acc->flag, conflicts in acc->ckey.
 // Same partition, views and classification as the solver's sweep.
@@ -1087,10 +1169,11 @@ __global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc)
 {
     extern __shared__ unsigned long long smem_raw[];
     uint32_t *vbase = reinterpret_cast<uint32_t *>(smem_raw + D.WW + 32) + 16;
-    const View V = make_view(D, vbase);
+    const View V = make_view(D, vbase, blockIdx.x);
     view_reload(D, V, 0u);
     __syncthreads();
-    SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu};
+    SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
+               (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
     sweep(X, 0u);
 }
 
@@ -1114,6 +1197,20 @@ cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStr
     Dev copy = D;
     void *args[] = {(void *)&copy};
     return cudaLaunchCooperativeKernel((void *)solve_kernel, dim3(grid), dim3(block), args, smem, st);
+}
+
+cudaError_t batch_configure(size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem);
+}
+
+cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
+                         size_t smem, cudaStream_t st)
+{
+    batch_kernel<<<grid, 256, smem, st>>>(devs, order, n, queue);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st)
