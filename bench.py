@@ -48,6 +48,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample length")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="programs of the batched workload (config-4 family); 0 = skip")
+    ap.add_argument("--batch-conflicts", type=int, default=100, help="per-program conflict budget")
     ap.add_argument("--sweep-only", type=int, default=0,
                     help="profiling aid: load the program and run this many standalone sweeps")
     return ap.parse_args()
@@ -111,6 +114,13 @@ class _Clocks:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
         return dict(sm_mhz=sm[len(sm) // 2] if sm else None, sm_max_mhz=max(mx) if mx else None,
                     reasons=reasons, samples=len(sm))
+
+
+def _plain(o):
+    """numpy scalars and arrays in the JSON line"""
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    return str(o)
 
 
 def _peaks():
@@ -203,7 +213,8 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.synchronize(dev)
 
     totals = dict(literal_checks=0, propagations=0, decisions=0, conflicts=0, rounds=0,
-                  ns_total=0, ns_sweep=0, ns_analysis=0, ns_decision=0, ns_stability=0)
+                  ns_total=0, ns_sweep=0, ns_analysis=0, ns_decision=0, ns_stability=0,
+                  ns_buckets=0, ns_learned=0, ns_barrier=0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     statuses = []
     barrier()
@@ -244,21 +255,28 @@ def run_ours(a, rank, world, local_rank):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peak else None,
                 "note": "store of 32 MB is L2-resident within a step; achieved counts 4 B per literal check"}
 
-    # sweep kernel alone, one launch = one propagate-and-check pass over the store
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(3):
-        P.sweep_once()
-    n_sw = 20
-    e0.record(stream)
-    for _ in range(n_sw):
-        P.sweep_once()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    sw_ms = e0.elapsed_time(e1) / n_sw
+    # sweep kernel alone: one launch loads the shared-memory views once and
+    # makes K passes; per-pass time = (t(K+1) - t(1)) / K
     st = P.stats()
-    sweep = {"ms_per_launch": sw_ms, "store_bytes": st["store_bytes"],
-             "achieved_gbs": st["store_bytes"] / (sw_ms / 1e3) / 1e9,
-             "frac_of_hbm": (st["store_bytes"] / (sw_ms / 1e3) / 1e9) / peak if peak else None}
+    sweep_bytes = 4 * (st["n_literals"] - st["n_unit_nogoods"])
+
+    def timed(passes, reps=5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        P.sweep(passes)
+        e0.record(stream)
+        for _ in range(reps):
+            P.sweep(passes)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    K = 16
+    t1, tk = timed(1), timed(K + 1)
+    per_pass = (tk - t1) / K
+    sweep = {"ms_per_pass": per_pass, "ms_view_load_and_one_pass": t1, "bytes_per_pass": sweep_bytes,
+             "achieved_gbs": sweep_bytes / (per_pass / 1e3) / 1e9,
+             "frac_of_hbm": (sweep_bytes / (per_pass / 1e3) / 1e9) / peak if peak else None,
+             "note": "store is L2-resident (32 MB < 126 MB L2)"}
 
     out = None
     if rank == 0:
@@ -279,6 +297,7 @@ def run_ours(a, rank, world, local_rank):
             d2h = words * 8 + 32
             e2e = {"value": e2e_checks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
+        batched = _batched(a, aspgpu, torch) if a.batch > 0 else None
         cpu = None if a.no_cpu else _cpu_baseline(prog, a.cpu_seconds)
         tsec = ms / 1e3
         out = {
@@ -291,13 +310,14 @@ def run_ours(a, rank, world, local_rank):
                        "store_bytes": st["store_bytes"], "l2": "flushed between steps (1 GiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": a.steps,
-            "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu,
+            "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "batched": batched,
             "clocks": clk.summary(),
             "search": {"statuses": statuses, "decisions_per_s": totals["decisions"] / tsec,
                        "propagations_per_s": totals["propagations"] / tsec,
                        "conflicts_per_s": totals["conflicts"] / tsec, "rounds_per_s": totals["rounds"] / tsec,
                        "device_ns": {k: totals[k] for k in ("ns_total", "ns_sweep", "ns_analysis",
-                                                           "ns_decision", "ns_stability")}},
+                                                           "ns_decision", "ns_stability", "ns_buckets",
+                                                           "ns_learned", "ns_barrier")}},
             "solver_src_sha": sha,
         }
     if world > 1:
@@ -305,7 +325,43 @@ def run_ours(a, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     if out is not None:
-        print(json.dumps(out), flush=True)
+        print(json.dumps(out, default=_plain), flush=True)
+
+
+def _batched(a, aspgpu, torch):
+    """Batched vs plain on the same programs: 4 rules per atom, atom counts
+    log-uniform in [200, 20000], seeds (4 << 32) | i; per-program conflict
+    budget.  solved = SAT or UNSAT within the budget."""
+    from synth.programs import batch_programs
+    progs = batch_programs(a.batch, rules_per_atom=4, config_id=4)
+    kw = dict(conflict_budget=a.batch_conflicts, time_budget_ms=20_000, deps_levels=1024,
+              learned_capacity=1 << 20)
+    P = [aspgpu.Program(p, **kw) for p in progs]
+    aspgpu.solve_batch(P[:8], max_models_each=1, cap_each=1)          # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, nm, _ = aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    solved_b = int(((st == 10) | (st == 20)).sum())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solved_p = 0
+    agree = 0
+    for i, q in enumerate(P):
+        s_, _, _ = q.solve(1, cap=1)
+        solved_p += s_ in (10, 20)
+        agree += int((s_ in (10, 20)) and (int(st[i]) in (10, 20)) and (s_ == int(st[i])))
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    for q in P:
+        q.close()
+    return {"workload": f"{a.batch} programs, 4 rules per atom, atoms log-uniform in [200, 20000], "
+                        f"conflict budget {a.batch_conflicts} per program, first answer set",
+            "batched": {"seconds": tb, "solved": solved_b, "solved_per_s": solved_b / tb},
+            "plain": {"seconds": tp, "solved": solved_p, "solved_per_s": solved_p / tp},
+            "both_solved_and_agree": agree,
+            "speedup_solved_per_s": (solved_b / tb) / (solved_p / tp) if solved_p else None}
 
 
 def run_sweeps(a):
@@ -317,8 +373,8 @@ def run_sweeps(a):
     prog = _program(a)
     P = aspgpu.Program(prog)
     P.propagate(np.zeros(P.n_vars, np.int8))
-    for _ in range(a.sweep_only):
-        P.sweep_once()
+    for _ in range(3):
+        P.sweep(a.sweep_only)
     torch.cuda.synchronize()
     print(json.dumps({"sweeps": a.sweep_only, "store_bytes": P.stats()["store_bytes"]}))
 

@@ -85,6 +85,8 @@ typedef struct {
     int64_t learned, learned_literals, loop_nogoods, models;
     int64_t max_level;
     int64_t ns_total, ns_sweep, ns_analysis, ns_decision, ns_stability; /* device time */
+    int64_t ns_buckets, ns_learned, ns_barrier; /* CTA 0: static buckets, long and learned
+                                                   nogoods, waiting at phase barriers */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */
@@ -143,10 +145,11 @@ const char *asp_last_error(void);
  * it may violate nogoods. */
 int asp_debug_propagate(asp_prog *p, const int8_t *partial, int8_t *closure, int32_t *conflict);
 
-/* One propagate-and-check sweep over the whole static store against the
- * current device assignment, without committing anything (used to time the
- * sweep kernel in isolation).  Enqueued on the program's stream. */
-int asp_sweep_once(asp_prog *p);
+/* Propagate-and-check sweeps over the whole static store against the
+ * current device assignment, without claiming anything (used to time the
+ * sweep in isolation): one launch loads each CTA's shared-memory view once,
+ * then makes `passes` full passes.  Enqueued on the program's stream. */
+int asp_sweep(asp_prog *p, int32_t passes);
 
 /* Copy of the state after the last solve or debug call, for consistency
  * checks: trail (n_trail variables in assignment order), per variable

@@ -43,11 +43,12 @@ class Stats(C.Structure):
         "n_unit_nogoods", "n_long_nogoods", "store_bytes", "rounds", "literal_checks",
         "propagations", "conflicts", "decisions", "completions", "learned",
         "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
-        "ns_sweep", "ns_analysis", "ns_decision", "ns_stability")]
+        "ns_sweep", "ns_analysis", "ns_decision", "ns_stability", "ns_buckets", "ns_learned",
+        "ns_barrier")]
 
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
-           "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep_once",
+           "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
            "asp_debug_state", "asp_debug_nogood", "asp_propagate_noalloc"]
 
 
@@ -86,8 +87,8 @@ def lib(build_if_missing: bool = True):
         L.asp_last_error.restype = C.c_char_p
         L.asp_debug_propagate.argtypes = [vp, vp, vp, vp]
         L.asp_debug_propagate.restype = C.c_int
-        L.asp_sweep_once.argtypes = [vp]
-        L.asp_sweep_once.restype = C.c_int
+        L.asp_sweep.argtypes = [vp, C.c_int32]
+        L.asp_sweep.restype = C.c_int
         L.asp_debug_state.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         L.asp_debug_state.restype = C.c_int
         L.asp_debug_nogood.argtypes = [vp, C.c_uint32, vp, i64]
@@ -210,8 +211,8 @@ class Program:
         pointers); enqueued on the program's stream.  Returns the ABI code."""
         return lib().asp_propagate_noalloc(self.handle, d_partial, d_closure, d_conflict)
 
-    def sweep_once(self):
-        _check(lib().asp_sweep_once(self.handle))
+    def sweep(self, passes: int = 1):
+        _check(lib().asp_sweep(self.handle, int(passes)))
 
     def stats(self) -> dict:
         s = Stats()

@@ -14,7 +14,8 @@
 namespace aspgpu {
 cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st,
+                         uint32_t passes);
 cudaError_t batch_configure(size_t smem, int *blocks_per_sm);
 cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
                          size_t smem, cudaStream_t st);
@@ -411,6 +412,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.models = (int64_t)s.models; o.max_level = (int64_t)s.max_level;
     o.ns_total = (int64_t)s.ns_total; o.ns_sweep = (int64_t)s.ns_sweep; o.ns_analysis = (int64_t)s.ns_analysis;
     o.ns_decision = (int64_t)s.ns_decision; o.ns_stability = (int64_t)s.ns_stab;
+    o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
 }
 
 extern "C" {
@@ -538,14 +540,14 @@ int asp_debug_propagate(asp_prog *p, const int8_t *partial, int8_t *closure, int
     return ASP_OK;
 }
 
-int asp_sweep_once(asp_prog *p)
+int asp_sweep(asp_prog *p, int32_t passes)
 {
-    if (!p) return fail(ASP_E_ARG, "bad argument");
+    if (!p || passes < 1) return fail(ASP_E_ARG, "bad argument");
     Acc a;
     a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
     cudaError_t e = cudaMemcpyAsync(p->d_sweep_acc, &a, sizeof(a), cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep reset");
-    e = launch_sweep(p->D, p->d_sweep_acc, p->grid, p->block, p->smem, p->stream);
+    e = launch_sweep(p->D, p->d_sweep_acc, p->grid, p->block, p->smem, p->stream, (uint32_t)passes);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     return ASP_OK;
 }

@@ -63,6 +63,9 @@ struct DevStats {
     unsigned long long learned, learned_lits, loops, models, max_level;
     unsigned long long ns_total, ns_sweep, ns_analysis, ns_decision, ns_stab;
     unsigned long long phases, pad;
+    // time inside sweeps seen by CTA 0: static buckets, long and learned
+    // nogoods, and waiting at the phase barrier
+    unsigned long long ns_buckets, ns_learned, ns_barrier, pad2;
 };
 
 struct Barrier { unsigned int count, gen, err, pad; };

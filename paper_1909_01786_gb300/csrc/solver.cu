@@ -471,14 +471,16 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
     const Dev &D = *X.D;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t G1 = D.G + 1u;
+    const bool timer = X.cta == 0 && threadIdx.x == 0 && X.do_claim;
+    const unsigned long long t0 = timer ? globaltimer_ns() : 0ull;
 #pragma unroll 1
     for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
         const uint32_t b0 = __ldg(D.cta_boff + L * G1 + X.cta);
         const uint32_t b1 = __ldg(D.cta_boff + L * G1 + X.cta + 1u);
         if (b1 <= b0) continue;
         switch (L) {
-        case 2: run_bucket<2, 4>(X, b0, b1); break;
-        case 3: run_bucket<3, 2>(X, b0, b1); break;
+        case 2: run_bucket<2, 8>(X, b0, b1); break;
+        case 3: run_bucket<3, 4>(X, b0, b1); break;
         case 4: run_bucket<4, 2>(X, b0, b1); break;
         case 5: run_bucket<5, 1>(X, b0, b1); break;
         case 6: run_bucket<6, 1>(X, b0, b1); break;
@@ -494,12 +496,18 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
         }
     }
     unsigned long long checks = 0;
+    const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
     const uint32_t nl = D.n_long + n_learned;
     for (uint32_t i = X.gw; i < nl; i += X.nw) {
         uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
         classify_long(X, id, checks);
     }
     if (lane == 0 && checks) atomicAdd(&X.acc->checks, checks);
+    if (timer) {
+        const unsigned long long t2 = globaltimer_ns();
+        D.stats->ns_buckets += t1 - t0;
+        D.stats->ns_learned += t2 - t1;
+    }
 }
 
 // bitmap word w of "every decision level 2..L" (CompleteAssignment reading)
@@ -1093,7 +1101,9 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             D.stats->phases += 1;
             __threadfence();
         }
+        const unsigned long long tb0 = (cta0 && threadIdx.x == 0) ? globaltimer_ns() : 0ull;
         if (!group_sync<BATCH>(D)) break;
+        if (cta0 && threadIdx.x == 0) D.stats->ns_barrier += globaltimer_ns() - tb0;
     }
     if (leader) {
         const Ctl F = sC;
@@ -1165,13 +1175,18 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const ui
 // One sweep over the static store without claiming (timing the sweep kernel
 // in isolation): counts unit nogoods in acc->flag, conflicts in acc->ckey.
 // Same partition, views and classification as the solver's sweep.
-__global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc)
+__global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc, uint32_t passes)
 {
     extern __shared__ unsigned long long smem_raw[];
     uint32_t *vbase = reinterpret_cast<uint32_t *>(smem_raw + D.WW + 32) + 16;
     const View V = make_view(D, vbase, blockIdx.x);
     view_reload(D, V, 0u);
     __syncthreads();
+    for (uint32_t pass = 1; pass < passes; pass++) {
+        SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
+                   (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
+        sweep(X, 0u);
+    }
     SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
                (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
     sweep(X, 0u);
@@ -1183,11 +1198,16 @@ __global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc)
 
 namespace aspgpu {
 
+// The dynamic shared-memory limit is a property of the kernel, shared by
+// every program: it is set to the largest size any program may use, and
+// occupancy is computed for this program's own size.
+constexpr int MAX_DYN_SMEM = 220 * 1024;
+
 cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block, smem);
 }
@@ -1201,7 +1221,7 @@ cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStr
 
 cudaError_t batch_configure(size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem);
 }
@@ -1213,9 +1233,10 @@ cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, uns
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st)
+cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st,
+                         uint32_t passes)
 {
-    sweep_kernel<<<grid, block, smem, st>>>(D, acc);
+    sweep_kernel<<<grid, block, smem, st>>>(D, acc, passes);
     return cudaGetLastError();
 }
 
