@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--batch", type=int, default=256,
                     help="programs of the batched workload (config-4 family); 0 = skip")
     ap.add_argument("--batch-conflicts", type=int, default=100, help="per-program conflict budget")
+    ap.add_argument("--learned", type=int, default=256,
+                    help="held-out programs for the learned-heuristic comparison; 0 = skip")
+    ap.add_argument("--learned-train", type=int, default=1024, help="training programs (traces)")
     ap.add_argument("--sweep-only", type=int, default=0,
                     help="profiling aid: load the program and run this many standalone sweeps")
     return ap.parse_args()
@@ -298,6 +301,7 @@ def run_ours(a, rank, world, local_rank):
             e2e = {"value": e2e_checks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
         batched = _batched(a, aspgpu, torch) if a.batch > 0 else None
+        learned = _learned(a, aspgpu, torch) if a.learned > 0 else None
         cpu = None if a.no_cpu else _cpu_baseline(prog, a.cpu_seconds)
         tsec = ms / 1e3
         out = {
@@ -311,6 +315,7 @@ def run_ours(a, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": a.steps,
             "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "batched": batched,
+            "learned_heuristic": learned,
             "clocks": clk.summary(),
             "search": {"statuses": statuses, "decisions_per_s": totals["decisions"] / tsec,
                        "propagations_per_s": totals["propagations"] / tsec,
@@ -362,6 +367,67 @@ def _batched(a, aspgpu, torch):
             "plain": {"seconds": tp, "solved": solved_p, "solved_per_s": solved_p / tp},
             "both_solved_and_agree": agree,
             "speedup_solved_per_s": (solved_b / tb) / (solved_p / tp) if solved_p else None}
+
+
+def _a11_programs(count, first_index):
+    """Half random programs (4 rules per atom, atoms log-uniform in
+    [200, 2000]), half 3-colourings of G(n, 4.5/(n-1)) with n in [40, 400]."""
+    from synth.programs import batch_programs, coloring_program, batch_sizes
+    half = count // 2
+    progs = batch_programs(half, rules_per_atom=4, config_id=5, first_index=first_index, lo=200, hi=2000)
+    _, ns = batch_sizes(count - half, lo=40, hi=400, config_id=6, first_index=first_index)
+    progs += [coloring_program(int(n), 4.5, seed_index=first_index + i) for i, n in enumerate(ns)]
+    return progs
+
+
+def _learned(a, aspgpu, torch):
+    """Learned vs plain decision heuristic on held-out programs, both batched,
+    same per-program conflict budget; training on traces of the plain
+    heuristic on disjoint seeds."""
+    from paper_1909_01786_gb300 import heuristic as H
+    budget = a.batch_conflicts
+    t0 = time.perf_counter()
+    X, y = H.collect_traces(_a11_programs(a.learned_train, 10**6), conflict_budget=budget)
+    w, tstats = H.fit(X, y)
+    t_train = time.perf_counter() - t0
+    H.save(w, os.path.join(ROOT, "gpurun_out", "heuristic_mlp.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+           else os.devnull, **tstats)
+    evalp = _a11_programs(a.learned, 2 * 10**6)
+    out = {}
+    for name, kw in (("plain", dict(heuristic=0)), ("learned", dict(heuristic=2, mlp_weights=w))):
+        P = [aspgpu.Program(p, conflict_budget=budget, time_budget_ms=20_000, deps_levels=1024,
+                            learned_capacity=1 << 20, **kw) for p in evalp]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, nm, models = aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        dec = sum(q.stats()["decisions"] for q in P)
+        con = sum(q.stats()["conflicts"] for q in P)
+        solved = int(((st == 10) | (st == 20)).sum())
+        out[name] = {"seconds": dt, "solved": solved, "solved_per_s": solved / dt,
+                     "decisions": int(dec), "conflicts": int(con), "statuses": st.copy(), "models": models}
+        for q in P:
+            q.close()
+    # zero mismatches: where both decided they agree; models are answer sets
+    import oracle
+    sp, sl = out["plain"]["statuses"], out["learned"]["statuses"]
+    both = ((sp == 10) | (sp == 20)) & ((sl == 10) | (sl == 20))
+    mism = int((sp[both] != sl[both]).sum())
+    checked = bad = 0
+    for name in ("plain", "learned"):
+        for i, m in enumerate(out[name]["models"]):
+            if len(m):
+                checked += 1
+                bad += not oracle.is_answer_set(evalp[i], m[0])
+    for name in ("plain", "learned"):
+        del out[name]["statuses"], out[name]["models"]
+    return {"workload": f"{a.learned} held-out programs (half random, 4 rules per atom, 200-2000 atoms; "
+                        f"half 3-colourings, 40-400 vertices), conflict budget {budget}, batched",
+            "training": {"programs": a.learned_train, "seconds": t_train, **tstats},
+            **out, "status_mismatches": mism, "models_checked": checked, "invalid_models": bad,
+            "speedup_solved_per_s": (out["learned"]["solved_per_s"] / out["plain"]["solved_per_s"])
+            if out["plain"]["solved"] else None}
 
 
 def run_sweeps(a):

@@ -54,6 +54,10 @@ extern "C" {
 
 #define ASP_HEUR_OCCURRENCE 0 /* static: occurrence count of the head (Section 4) */
 #define ASP_HEUR_ACTIVITY 1   /* occurrence count plus activity bumped by conflicts */
+#define ASP_HEUR_LEARNED 2    /* log1p(head occurrences) + log sigmoid(MLP logit) (not in the paper) */
+
+#define ASP_MLP_FEATURES 16   /* inputs of the learned heuristic per candidate rule */
+#define ASP_MLP_PARAMS 1153   /* W1[64][16], b1[64], w2[64], b2 */
 
 typedef struct asp_prog asp_prog; /* opaque, owned by the library */
 
@@ -72,6 +76,11 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *ctx);
     void (*dev_free)(void *ptr, size_t bytes, void *ctx);
     void *alloc_ctx;
+    /* learned heuristic: ASP_MLP_PARAMS host floats, copied at load (used
+       when heuristic = ASP_HEUR_LEARNED; stored as bf16) */
+    const float *mlp_weights;
+    /* record up to this many decisions per solve for asp_trace; 0 = none */
+    int64_t trace_capacity;
 } asp_options;
 
 typedef struct {
@@ -163,6 +172,32 @@ int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *leve
 /* Literals of nogood `id` (a reason or learned id) as (var << 1 | sign),
  * sign 1 = F; returns the length, writes at most cap literals. */
 int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap);
+
+/* ---- learned decision heuristic (not in the paper) ------------------------
+ * Decision traces of the last solve, for training: at every Decision step
+ * about one applicable rule in eight is sampled, giving one row of
+ * ASP_MLP_FEATURES floats (8 static features of the rule, log1p activity,
+ * B- atoms unassigned and false, level/64, log1p conflicts, assigned
+ * fraction, 0, 0) and a label: 1 if the rule's body holds in the first
+ * answer set the search found, 0 if not, -1 if no answer set was found.
+ * rules (may be NULL) receives each row's rule index j (solver numbering,
+ * see Conventions).  Host buffers of cap rows; returns the number of rows
+ * (at most trace_capacity), or a negative ASP_E_*. */
+int64_t asp_trace(asp_prog *p, float *features, int32_t *labels, int32_t *rules, int64_t cap);
+
+/* Train the heuristic's MLP (16 -> 64 ReLU -> 1, logistic output) on the
+ * device: minibatches of 4096, SGD with momentum 0.9, binary cross-entropy.
+ * features: host [n][ASP_MLP_FEATURES]; labels: host [n] in {0, 1};
+ * weights: host [ASP_MLP_PARAMS], initial values in, trained values out.
+ * Blocks until done.  Uses the current device and allocates its own
+ * buffers. */
+int asp_train_mlp(const float *features, const float *labels, int64_t n, int32_t epochs,
+                  float learning_rate, float *weights);
+
+/* Scores of n feature rows under the given weights, computed on the device
+ * exactly as the Decision step does (weights rounded to bf16, fp32
+ * accumulation).  Host buffers: features [n][ASP_MLP_FEATURES], scores [n]. */
+int asp_mlp_score(const float *weights, const float *features, int64_t n, float *scores);
 
 /* ---- allocation-free propagation ---------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers

@@ -16,6 +16,8 @@ import numpy as np
 from . import build as _build
 
 ASP_OK, ASP_E_CAPACITY = 0, -5
+MLP_FEATURES, MLP_PARAMS = 16, 1153
+HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED = 0, 1, 2
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 R_DECISION, R_COMPLETE, R_INPUT = 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD
 
@@ -34,7 +36,8 @@ class Options(C.Structure):
                 ("conflict_budget", C.c_int64), ("time_budget_ms", C.c_int64),
                 ("learned_capacity", C.c_int64), ("grid_ctas", C.c_int32),
                 ("block_threads", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
+                ("mlp_weights", C.c_void_p), ("trace_capacity", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -49,7 +52,8 @@ class Stats(C.Structure):
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
-           "asp_debug_state", "asp_debug_nogood", "asp_propagate_noalloc"]
+           "asp_debug_state", "asp_debug_nogood", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
+           "asp_mlp_score"]
 
 
 def library_path() -> str:
@@ -95,6 +99,12 @@ def lib(build_if_missing: bool = True):
         L.asp_debug_nogood.restype = i64
         L.asp_propagate_noalloc.argtypes = [vp, vp, vp, vp]
         L.asp_propagate_noalloc.restype = C.c_int
+        L.asp_trace.argtypes = [vp, vp, vp, vp, i64]
+        L.asp_trace.restype = i64
+        L.asp_train_mlp.argtypes = [vp, vp, i64, i32, C.c_float, vp]
+        L.asp_train_mlp.restype = C.c_int
+        L.asp_mlp_score.argtypes = [vp, vp, i64, vp]
+        L.asp_mlp_score.restype = C.c_int
         _lib = L
         return L
 
@@ -136,12 +146,19 @@ class Program:
     """A ground program loaded on the GPU (asp_load_ground)."""
 
     def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
-                 learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True):
+                 learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True,
+                 mlp_weights=None, trace_capacity=0):
         L = lib()
         self.n_atoms = int(prog.n_atoms)
         self._keep = []
         opt = Options()
         L.asp_default_options(C.byref(opt))
+        if mlp_weights is not None:
+            w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+            assert w.shape == (MLP_PARAMS,)
+            self._keep.append(w)
+            opt.mlp_weights = w.ctypes.data
+        opt.trace_capacity = int(trace_capacity)
         opt.heuristic, opt.deps_levels = heuristic, deps_levels
         opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
         opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads
@@ -211,6 +228,19 @@ class Program:
         pointers); enqueued on the program's stream.  Returns the ABI code."""
         return lib().asp_propagate_noalloc(self.handle, d_partial, d_closure, d_conflict)
 
+    def trace(self, cap: int = 1 << 16, with_rules: bool = False):
+        """Decision trace of the last solve: (features [n, 16], labels [n])
+        and, with_rules, the rule index of each row."""
+        f = np.zeros((max(cap, 1), MLP_FEATURES), np.float32)
+        y = np.zeros(max(cap, 1), np.int32)
+        r = np.zeros(max(cap, 1), np.int32)
+        n = lib().asp_trace(self.handle, f.ctypes.data, y.ctypes.data, r.ctypes.data, int(cap))
+        if n < 0:
+            raise AspError(n, lib().asp_last_error().decode())
+        if with_rules:
+            return f[:n].copy(), y[:n].copy(), r[:n].copy()
+        return f[:n].copy(), y[:n].copy()
+
     def sweep(self, passes: int = 1):
         _check(lib().asp_sweep(self.handle, int(passes)))
 
@@ -256,3 +286,23 @@ def solve_batch(programs, max_models_each: int = 1, cap_each: int = 1):
                                  caps.ctypes.data))
     models = [words_to_models(b[:min(int(k), cap_each)], p.n_atoms) for b, k, p in zip(bufs, nm, programs)]
     return st, nm, models
+
+
+def train_mlp(features: np.ndarray, labels: np.ndarray, weights: np.ndarray, epochs: int = 50,
+              learning_rate: float = 0.05) -> np.ndarray:
+    """asp_train_mlp: returns the trained weights (float32 [MLP_PARAMS])."""
+    X = np.ascontiguousarray(features, dtype=np.float32)
+    y = np.ascontiguousarray(labels, dtype=np.float32)
+    w = np.ascontiguousarray(weights, dtype=np.float32).copy()
+    _check(lib().asp_train_mlp(X.ctypes.data, y.ctypes.data, int(X.shape[0]), int(epochs),
+                               float(learning_rate), w.ctypes.data))
+    return w
+
+
+def mlp_score(weights: np.ndarray, features: np.ndarray) -> np.ndarray:
+    """asp_mlp_score: device scores of feature rows (bf16 weights, fp32 sums)."""
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    X = np.ascontiguousarray(features, dtype=np.float32)
+    out = np.zeros(X.shape[0], np.float32)
+    _check(lib().asp_mlp_score(w.ctypes.data, X.ctypes.data, int(X.shape[0]), out.ctypes.data))
+    return out

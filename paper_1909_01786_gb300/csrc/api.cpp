@@ -105,6 +105,9 @@ static T *upload(asp_prog *p, const std::vector<T> &v, int &rc)
     return d;
 }
 
+// shared memory for the heuristic's bf16 weights, after the view
+constexpr size_t MLP_SMEM_BYTES = ((2 * MLP_PARAMS + 15) / 16) * 16;
+
 // Grid size, the static partition of the buckets over the CTAs along groups
 // (an atom with its rules; a constraint), each CTA's slice of auxiliary
 // variables kept in shared memory, and the shared-memory layout.
@@ -112,7 +115,7 @@ static int plan_grid(asp_prog *p, const HostStore &H)
 {
     Dev &D = p->D;
     const size_t max_smem = 220 * 1024;
-    const size_t base_smem = 8ull * D.WW + 8ull * 32 + 4ull * 16;
+    const size_t base_smem = 8ull * D.WW + 8ull * 32 + 4ull * 16 + MLP_SMEM_BYTES;
     int per_sm = 0;
     cudaError_t e = solve_configure(p->block, max_smem, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "kernel configuration");
@@ -197,7 +200,7 @@ static int plan_batch(asp_prog *p, const HostStore &H)
     for (int L = 2; L <= BUCKET_MAX; L++) boff[L * 2 + 1] = (uint32_t)H.bucket_group[L].size();
     alo[0] = D1.na;
     an[0] = 3 * D1.J;
-    const size_t base = 8ull * D1.WW + 8ull * 32 + 4ull * 16;
+    const size_t base = 8ull * D1.WW + 8ull * 32 + 4ull * 16 + MLP_SMEM_BYTES;
     size_t aw = (D1.na + 15u) / 16u, xw = (an[0] + 15u) / 16u;
     D1.view_atoms = D1.na;
     if (base + 4 * (aw + xw) > BATCH_SMEM_BUDGET) {
@@ -289,6 +292,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.WW = WW;
     D.Wlevels = WW * 64u;
     D.heuristic = (uint32_t)std::max(0, p->opt.heuristic);
+    if (D.heuristic > 2) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
     p->n_nogoods = H.n_nogoods;
     p->n_literals = H.n_literals;
     p->n_units = (int64_t)H.units.size();
@@ -312,6 +316,25 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     if (rc == ASP_OK) D.rneg_off = upload(p, H.rneg_off, rc);
     if (rc == ASP_OK) D.rneg = upload(p, H.rneg, rc);
     if (rc == ASP_OK) D.score = upload(p, H.score, rc);
+    if (rc == ASP_OK) D.rfeat = upload(p, H.rfeat, rc);
+    if (rc == ASP_OK && D.heuristic == 2) {
+        if (!p->opt.mlp_weights) rc = fail(ASP_E_ARG, "learned heuristic without mlp_weights");
+        else {
+            // bf16 by round-to-nearest-even of the float bits
+            std::vector<uint16_t> w(MLP_PARAMS);
+            for (int i = 0; i < MLP_PARAMS; i++) {
+                uint32_t u;
+                std::memcpy(&u, p->opt.mlp_weights + i, 4);
+                w[i] = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+            }
+            D.mlp = upload(p, w, rc);
+        }
+    }
+    if (rc == ASP_OK && p->opt.trace_capacity > 0) {
+        D.trace_cap = (uint32_t)std::min<int64_t>(p->opt.trace_capacity, 1 << 24);
+        D.trace = (uint32_t *)dalloc(p, (size_t)D.trace_cap * TRACE_WORDS * 4);
+        if (!D.trace) rc = fail(ASP_E_OOM, "device allocation failed (trace)");
+    }
     auto alloc = [&](size_t bytes) -> void * {
         if (rc != ASP_OK) return nullptr;
         void *q = dalloc(p, bytes);
@@ -609,6 +632,29 @@ int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap)
     }
     for (int64_t i = 0; i < (int64_t)buf.size() && i < cap; i++) lits[i] = (int32_t)buf[i];
     return (int64_t)buf.size();
+}
+
+int64_t asp_trace(asp_prog *p, float *features, int32_t *labels, int32_t *rules, int64_t cap)
+{
+    if (!p || cap < 0 || (cap > 0 && (!features || !labels))) return fail(ASP_E_ARG, "bad argument");
+    if (!p->D.trace) return 0;
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    DevStats s;
+    e = cudaMemcpy(&s, p->D.stats, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "trace");
+    const int64_t n = std::min<int64_t>({(int64_t)s.trace_n, (int64_t)p->D.trace_cap, cap});
+    std::vector<uint32_t> rec((size_t)std::max<int64_t>(n, 1) * TRACE_WORDS);
+    if (n > 0) {
+        e = cudaMemcpy(rec.data(), p->D.trace, (size_t)n * TRACE_WORDS * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "trace");
+    }
+    for (int64_t i = 0; i < n; i++) {
+        std::memcpy(features + i * N_FEATURES, rec.data() + i * TRACE_WORDS, N_FEATURES * 4);
+        labels[i] = rec[(size_t)i * TRACE_WORDS + 19] ? (int32_t)rec[(size_t)i * TRACE_WORDS + 18] : -1;
+        if (rules) rules[i] = (int32_t)rec[(size_t)i * TRACE_WORDS + 16];
+    }
+    return n;
 }
 
 int asp_solve_batch(int32_t n, asp_prog *const *progs, int64_t max_models_each,

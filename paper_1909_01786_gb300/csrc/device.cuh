@@ -36,13 +36,22 @@ enum Mode : uint32_t { MODE_SOLVE = 0, MODE_PROPAGATE = 1 };
 
 constexpr unsigned long long NO_KEY = ~0ull;
 
+// learned heuristic: 16 features -> 64 hidden (ReLU) -> 1, parameters
+// W1[64][16], b1[64], w2[64], b2
+constexpr int N_FEATURES = 16, N_HIDDEN = 64;
+constexpr int MLP_PARAMS = N_FEATURES * N_HIDDEN + 2 * N_HIDDEN + 1;
+// trace record: 16 feature words (float bits), rule, level, label, labelled
+constexpr int TRACE_WORDS = 20;
+// a candidate rule is sampled into the trace when its hash has these bits clear
+constexpr uint32_t TRACE_SAMPLE_MASK = 7u;
+
 struct Ctl {              // double-buffered control block (phase parity)
     uint32_t op, cdl, tc, tb;   // tc: trail entries committed; tb: base of last claims
     // (a claim's level, reason and dependency bitmap are written when it is
     // made; "committing" only clears its fresh bit and makes it visible to
     // every CTA's shared-memory view)
     uint32_t round, clean, target, conf_id;
-    uint32_t n_learned, lfill, stab_first, idle_completes;
+    uint32_t n_learned, lfill, stab_first, trace_n;
     long long n_models;
     int32_t status, err;
     int32_t conflict, pad;
@@ -66,6 +75,7 @@ struct DevStats {
     // time inside sweeps seen by CTA 0: static buckets, long and learned
     // nogoods, and waiting at the phase barrier
     unsigned long long ns_buckets, ns_learned, ns_barrier, pad2;
+    unsigned int trace_n, pad4;    // trace records written (atomic)
 };
 
 struct Barrier { unsigned int count, gen, err, pad; };
@@ -94,6 +104,12 @@ struct Dev {
     const int32_t *rule_head;
     const uint32_t *rpos_off, *rpos, *rneg_off, *rneg, *score;
     uint32_t *act;
+    // learned decision heuristic (heuristic 2): static rule features
+    // [J][8], MLP weights (bf16 bits, MLP_PARAMS), decision trace
+    const float *rfeat;
+    const uint16_t *mlp;
+    uint32_t *trace;          // [trace_cap][TRACE_WORDS]
+    uint32_t trace_cap, pad3;
     uint32_t *asg;
     int32_t *dl;
     uint32_t *reason;

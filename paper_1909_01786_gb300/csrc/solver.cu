@@ -21,10 +21,12 @@
 // can resolve within one sweep; other CTAs see the claim after the next
 // barrier.  Long and learned nogoods are classified by one warp each (ballot
 // and popc over lanes), against the global codes.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "device.cuh"
+#include "mlp.cuh"
 #include "store.h"
 
 namespace aspgpu {
@@ -556,12 +558,48 @@ struct Smem {
     unsigned long long *bm;     // [WW] conflict bitmap
     unsigned long long *red;    // [32]
     uint32_t *misc;             // [16]
+    const __nv_bfloat16 *mlp;   // [MLP_PARAMS] after the view (heuristic 2)
 };
+
+// The 16 features of candidate rule j (inputs of the learned heuristic):
+// its 8 static features, then log1p activity, B- atoms still unassigned and
+// already false, decision level / 64, log1p conflicts so far, fraction of
+// variables assigned, two zeros.
+__device__ __forceinline__ void cand_features(const Dev &D, uint32_t j, uint32_t cdl, uint32_t tend, float *x)
+{
+    const float *sf = D.rfeat + (size_t)j * 8u;
+#pragma unroll
+    for (int q = 0; q < 8; q++) x[q] = __ldg(sf + q);
+    x[8] = log1pf((float)__ldcg(D.act + j));
+    uint32_t un = 0, fa = 0;
+    for (uint32_t q = __ldg(D.rneg_off + j); q < __ldg(D.rneg_off + j + 1); q++) {
+        const uint32_t a = __ldg(D.rneg + q);
+        const uint32_t v = (__ldcg(D.asg + (a >> 3)) >> ((a & 7u) * 4u)) & 3u;
+        un += v == 0u;
+        fa += v == V_F;
+    }
+    x[9] = (float)un;
+    x[10] = (float)fa;
+    x[11] = (float)cdl * (1.0f / 64.0f);
+    x[12] = log1pf((float)__ldcg(&D.stats->conflicts));
+    x[13] = (float)tend / (float)(D.nv ? D.nv : 1u);
+    x[14] = 0.0f;
+    x[15] = 0.0f;
+}
+
+// order-preserving map of a float to a positive 32-bit key
+__device__ __forceinline__ uint32_t float_key(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return u ? u : 1u;
+}
 
 // Decision (Section 2 / Section 4): among rules whose head is unassigned,
 // with t_r true, n_r not false and b_r unassigned (applicable), pick the
 // highest score, ties to the lowest rule index.
-__device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, uint32_t gtid, uint32_t nthreads)
+__device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, uint32_t gtid, uint32_t nthreads,
+                                       uint32_t cdl, uint32_t tend)
 {
     unsigned long long best = 0;
     for (uint32_t j = gtid; j < D.J; j += nthreads) {
@@ -572,10 +610,42 @@ __device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, ui
         uint32_t ct = nib(__ldcg(D.asg + (t >> 3)), t) & 3u;
         uint32_t cn = nib(__ldcg(D.asg + (n >> 3)), n) & 3u;
         if (ch == 0u && cb == 0u && ct == V_T && cn != V_F) {
-            unsigned long long sc = __ldg(D.score + j);
-            if (D.heuristic == 1) sc += (unsigned long long)__ldcg(D.act + j) * 8ull;
-            if (sc > 0x7FFFFFFFull) sc = 0x7FFFFFFFull;
-            unsigned long long key = ((sc + 1ull) << 32) | (0xFFFFFFFFull - j);
+            unsigned long long key;
+            if (D.trace) {
+                // sample about one candidate in eight per decision point
+                uint32_t hsh = (j * 0x9E3779B1u) ^ (cdl * 0x85EBCA77u) ^ (tend * 0xC2B2AE3Du);
+                hsh ^= hsh >> 15;
+                hsh *= 0x2C1B3C6Du;
+                hsh ^= hsh >> 12;
+                if ((hsh & TRACE_SAMPLE_MASK) == 0u) {
+                    const uint32_t r = atomicAdd(&D.stats->trace_n, 1u);
+                    if (r < D.trace_cap) {
+                        float x[N_FEATURES];
+                        cand_features(D, j, cdl, tend, x);
+                        uint32_t *rec = D.trace + (size_t)r * TRACE_WORDS;
+                        for (int q = 0; q < N_FEATURES; q++) rec[q] = __float_as_uint(x[q]);
+                        rec[16] = j;
+                        rec[17] = cdl;
+                        rec[18] = 0u;
+                        rec[19] = 0u;
+                    }
+                }
+            }
+            if (D.heuristic == 2) {
+                // plain score (log1p occurrences of the head, feature 0) plus
+                // the log of the learned probability that the rule's body
+                // holds in an answer set
+                float x[N_FEATURES];
+                cand_features(D, j, cdl, tend, x);
+                const float z = mlp_score(S.mlp, x);
+                const float log_p = z >= 0.0f ? -log1pf(__expf(-z)) : z - log1pf(__expf(z));
+                key = ((unsigned long long)float_key(x[0] + log_p) << 32) | (0xFFFFFFFFull - j);
+            } else {
+                unsigned long long sc = __ldg(D.score + j);
+                if (D.heuristic == 1) sc += (unsigned long long)__ldcg(D.act + j) * 8ull;
+                if (sc > 0x7FFFFFFFull) sc = 0x7FFFFFFFull;
+                key = ((sc + 1ull) << 32) | (0xFFFFFFFFull - j);
+            }
             best = key > best ? key : best;
         }
     }
@@ -710,6 +780,7 @@ __device__ __forceinline__ Smem make_smem(const Dev &D, unsigned long long *raw)
     S.bm = raw;
     S.red = S.bm + D.WW;
     S.misc = reinterpret_cast<uint32_t *>(S.red + 32);
+    S.mlp = reinterpret_cast<const __nv_bfloat16 *>(S.misc + 16 + D.view_words);
     return S;
 }
 
@@ -740,6 +811,10 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     if (leader) { t_start = globaltimer_ns(); t_phase = t_start; }
 
     if (threadIdx.x == 0) ldcg_copy(&sC, D.ctl);
+    if (D.heuristic == 2) {
+        uint16_t *w = const_cast<uint16_t *>(reinterpret_cast<const uint16_t *>(S.mlp));
+        for (uint32_t i = threadIdx.x; i < (uint32_t)MLP_PARAMS; i += blockDim.x) w[i] = __ldg(D.mlp + i);
+    }
     __syncthreads();
     view_reload(D, V, 4u << (sC.round & 1u));
     __syncthreads();
@@ -833,7 +908,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     break;
                 }
                 kind = 2;
-                decide(D, S, acc, gtid, nthreads);
+                decide(D, S, acc, gtid, nthreads, C.cdl, tend);
                 if (leader) N.op = OP_APPLY;
                 break;
             }
@@ -976,6 +1051,16 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 // answer set: record it, then block it with the decision literals
                 const long long row = C.n_models;
                 const uint32_t words = (D.na + 63u) >> 6;
+                if (D.trace && row == 0) {
+                    // label each sampled candidate: does its body hold in the answer set
+                    const uint32_t nrec = min(__ldcg(&D.stats->trace_n), D.trace_cap);
+                    for (uint32_t r = gtid; r < nrec; r += nthreads) {
+                        uint32_t *rec = D.trace + (size_t)r * TRACE_WORDS;
+                        const uint32_t b = D.na + 3u * rec[16];
+                        rec[18] = (nib(__ldcg(D.asg + (b >> 3)), b) & 3u) == V_T ? 1u : 0u;
+                        rec[19] = 1u;
+                    }
+                }
                 if (row < D.models_cap) {
                     for (uint32_t w = gtid; w < words; w += nthreads) {
                         unsigned long long m = 0;

@@ -14,6 +14,7 @@
 #include "store.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "aspgpu.h"
@@ -169,6 +170,29 @@ int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     for (uint32_t u : S.units) count(u);
     S.score.resize(J);
     for (uint32_t j = 0; j < J; j++) S.score[j] = occ[S.rule_head[j]];
+
+    // static features of each rule (inputs of the learned heuristic):
+    // log1p occurrences of the head, |B+|, |B-|, log1p |rules(head)|,
+    // log1p positive and negative body occurrences of the head, log1p of the
+    // positive body occurrences of the atoms the rule falsifies, 1
+    std::vector<uint32_t> posocc((size_t)n_atoms + 1, 0), negocc((size_t)n_atoms + 1, 0);
+    for (uint32_t a : S.rpos) posocc[a]++;
+    for (uint32_t a : S.rneg) negocc[a]++;
+    S.rfeat.assign((size_t)J * RULE_STATIC_FEATURES, 0.0f);
+    for (uint32_t j = 0; j < J; j++) {
+        float *f = S.rfeat.data() + (size_t)j * RULE_STATIC_FEATURES;
+        const uint32_t h = (uint32_t)S.rule_head[j];
+        uint64_t blocked = 0;
+        for (uint32_t k = S.rneg_off[j]; k < S.rneg_off[j + 1]; k++) blocked += posocc[S.rneg[k]];
+        f[0] = std::log1p((float)occ[h]);
+        f[1] = (float)(S.rpos_off[j + 1] - S.rpos_off[j]);
+        f[2] = (float)(S.rneg_off[j + 1] - S.rneg_off[j]);
+        f[3] = std::log1p((float)(first[h + 1] - first[h]));
+        f[4] = std::log1p((float)posocc[h]);
+        f[5] = std::log1p((float)negocc[h]);
+        f[6] = std::log1p((float)blocked);
+        f[7] = 1.0f;
+    }
 
     for (int L = 2; L <= BUCKET_MAX; L++)
         if (S.bucket_group[L].size() >= (1u << 27)) { err = "too many nogoods of one length (>= 2^27)"; return ASP_E_RANGE; }

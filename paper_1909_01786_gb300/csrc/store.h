@@ -47,7 +47,11 @@ struct HostStore {
     std::vector<int32_t> rule_head;                  // [n_headed]
     std::vector<uint32_t> rpos_off, rpos, rneg_off, rneg;
     std::vector<uint32_t> score;                     // static decision score per headed rule
+    std::vector<float> rfeat;                        // [n_headed][8] static features of each rule
 };
+
+// static features per rule for the learned decision heuristic
+constexpr int RULE_STATIC_FEATURES = 8;
 
 // Returns 0 or a negative ASP_E_* code with a message in err.
 int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
