@@ -378,13 +378,28 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
     }
 }
 
-template <int L, int U>
-__device__ __forceinline__ void run_bucket(const SweepCtx &X, uint32_t b0, uint32_t b1)
+// Groups of 32 nogoods per unit of work, by bucket length: about 16 literal
+// loads in flight per lane.
+__host__ __device__ constexpr uint32_t unit_groups(uint32_t L) { return L <= 2u ? 8u : L <= 4u ? 4u : L <= 8u ? 2u : 1u; }
+
+__device__ __forceinline__ void run_unit(const SweepCtx &X, uint32_t L, uint32_t k0, uint32_t k1)
 {
-    const uint32_t wid = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-    const uint32_t ntask = (b1 - b0 + 31u) >> 5;
-    for (uint32_t t0 = wid; t0 < ntask; t0 += nwb * (uint32_t)U)
-        bucket_tasks<L, U>(X, b0 + t0 * 32u, b1, nwb * 32u);
+    switch (L) {
+    case 2: bucket_tasks<2, unit_groups(2)>(X, k0, k1, 32u); break;
+    case 3: bucket_tasks<3, unit_groups(3)>(X, k0, k1, 32u); break;
+    case 4: bucket_tasks<4, unit_groups(4)>(X, k0, k1, 32u); break;
+    case 5: bucket_tasks<5, unit_groups(5)>(X, k0, k1, 32u); break;
+    case 6: bucket_tasks<6, unit_groups(6)>(X, k0, k1, 32u); break;
+    case 7: bucket_tasks<7, unit_groups(7)>(X, k0, k1, 32u); break;
+    case 8: bucket_tasks<8, unit_groups(8)>(X, k0, k1, 32u); break;
+    case 9: bucket_tasks<9, unit_groups(9)>(X, k0, k1, 32u); break;
+    case 10: bucket_tasks<10, unit_groups(10)>(X, k0, k1, 32u); break;
+    case 11: bucket_tasks<11, unit_groups(11)>(X, k0, k1, 32u); break;
+    case 12: bucket_tasks<12, unit_groups(12)>(X, k0, k1, 32u); break;
+    case 13: bucket_tasks<13, unit_groups(13)>(X, k0, k1, 32u); break;
+    case 14: bucket_tasks<14, unit_groups(14)>(X, k0, k1, 32u); break;
+    default: bucket_tasks<15, unit_groups(15)>(X, k0, k1, 32u); break;
+    }
 }
 
 // A nogood of any length, one warp, lanes over literals (ballot/popc),
@@ -475,27 +490,34 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
     const uint32_t G1 = D.G + 1u;
     const bool timer = X.cta == 0 && threadIdx.x == 0 && X.do_claim;
     const unsigned long long t0 = timer ? globaltimer_ns() : 0ull;
-#pragma unroll 1
+    // Units of work (one bucket, unit_groups(L) consecutive groups of 32
+    // nogoods) are taken from a per-CTA counter, bucket after bucket, so
+    // every warp runs about the same number of load-gather-classify chains
+    // whatever the mix of lengths.
+    __shared__ unsigned int s_unit;
+    __syncthreads();                       // the previous sweep's warps are done with it
+    if (threadIdx.x == 0) s_unit = 0u;
+    __syncthreads();
+    uint32_t ubase[BUCKET_MAX + 2];
+    ubase[2] = 0u;
+#pragma unroll
     for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
+        const uint32_t n = __ldg(D.cta_boff + L * G1 + X.cta + 1u) - __ldg(D.cta_boff + L * G1 + X.cta);
+        const uint32_t groups = (n + 31u) >> 5, per = unit_groups(L);
+        ubase[L + 1] = ubase[L] + (groups + per - 1u) / per;
+    }
+    const uint32_t units = ubase[BUCKET_MAX + 1];
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(&s_unit, 1u);
+        u = __shfl_sync(FULL_MASK, u, 0);
+        if (u >= units) break;
+        uint32_t L = 2;
+#pragma unroll
+        for (uint32_t q = 3; q <= (uint32_t)BUCKET_MAX; q++) if (u >= ubase[q]) L = q;
         const uint32_t b0 = __ldg(D.cta_boff + L * G1 + X.cta);
         const uint32_t b1 = __ldg(D.cta_boff + L * G1 + X.cta + 1u);
-        if (b1 <= b0) continue;
-        switch (L) {
-        case 2: run_bucket<2, 8>(X, b0, b1); break;
-        case 3: run_bucket<3, 4>(X, b0, b1); break;
-        case 4: run_bucket<4, 2>(X, b0, b1); break;
-        case 5: run_bucket<5, 1>(X, b0, b1); break;
-        case 6: run_bucket<6, 1>(X, b0, b1); break;
-        case 7: run_bucket<7, 1>(X, b0, b1); break;
-        case 8: run_bucket<8, 1>(X, b0, b1); break;
-        case 9: run_bucket<9, 1>(X, b0, b1); break;
-        case 10: run_bucket<10, 1>(X, b0, b1); break;
-        case 11: run_bucket<11, 1>(X, b0, b1); break;
-        case 12: run_bucket<12, 1>(X, b0, b1); break;
-        case 13: run_bucket<13, 1>(X, b0, b1); break;
-        case 14: run_bucket<14, 1>(X, b0, b1); break;
-        default: run_bucket<15, 1>(X, b0, b1); break;
-        }
+        run_unit(X, L, b0 + (u - ubase[L]) * unit_groups(L) * 32u, b1);
     }
     unsigned long long checks = 0;
     const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
