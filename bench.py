@@ -33,7 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "nogood-literal checks/s"
 UNIT = "checks/s"
-WORKLOAD = "large random program: 100k atoms, 400k rules, body 1-4, negation 0.5, seed 0; first answer set, conflict budget per step"
+def workload(a):
+    return (f"large random program: {a.atoms // 1000}k atoms, {a.rules // 1000}k rules, body 1-4, "
+            "negation 0.5, seed 0; first answer set, conflict budget per step")
 
 
 def _args():
@@ -133,16 +135,18 @@ def _peaks():
         return {}
 
 
-def _traffic(kernel_src_sha):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+def _traffic(kernel_src_sha, checks_per_launch, atoms, rules):
+    """DRAM bytes per launch of the solve kernel from the committed ncu
+    capture, if it was taken on the current kernel source.  The capture ran a
+    shorter launch (smaller conflict budget) of the same workload; its bytes
+    per literal check are scaled to this launch's checks."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except OSError:
         return None
-    if t.get("solver_src_sha") != kernel_src_sha:
+    if t.get("solver_src_sha") != kernel_src_sha or (t.get("atoms"), t.get("rules")) != (atoms, rules):
         return None
-    return t.get("dram_bytes_per_launch")
+    return t["dram_bytes_per_literal_check"] * checks_per_launch
 
 
 def _src_sha():
@@ -171,7 +175,7 @@ def run_reference(a, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD + f"; oracle bounded to {per_step:.1f} s per step"},
+        "data": "synthetic", "config": {"workload": workload(a) + f"; oracle bounded to {per_step:.1f} s per step"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{a.steps} steps of {per_step:.1f} s CPU time each"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -251,12 +255,14 @@ def run_ours(a, rank, world, local_rank):
     peak = peaks.get("hbm_gbs")
     achieved = 4.0 * checks / (ms / 1e3) / 1e9          # algorithmic bytes: 4 B per literal check
     sha = _src_sha()
-    traffic = _traffic(sha)
+    traffic = _traffic(sha, checks / max(len(ev), 1), a.atoms, a.rules)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if peak else None,
                 "traffic": traffic, "kernel": "solve_kernel",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peak else None,
-                "note": "store of 32 MB is L2-resident within a step; achieved counts 4 B per literal check"}
+                "note": f"store of {P.stats()['store_bytes'] / 1e6:.0f} MB; achieved counts 4 B per literal check; "
+                        "traffic = DRAM bytes per literal check from an ncu capture of a 20-conflict launch "
+                        "of this workload x this launch's checks"}
 
     # sweep kernel alone: one launch loads the shared-memory views once and
     # makes K passes; per-pass time = (t(K+1) - t(1)) / K
@@ -279,7 +285,8 @@ def run_ours(a, rank, world, local_rank):
     sweep = {"ms_per_pass": per_pass, "ms_view_load_and_one_pass": t1, "bytes_per_pass": sweep_bytes,
              "achieved_gbs": sweep_bytes / (per_pass / 1e3) / 1e9,
              "frac_of_hbm": (sweep_bytes / (per_pass / 1e3) / 1e9) / peak if peak else None,
-             "note": "store is L2-resident (32 MB < 126 MB L2)"}
+             "note": (f"store of {st['store_bytes'] / 1e6:.0f} MB "
+                      + ("is L2-resident (< 126 MB L2)" if st["store_bytes"] < 126e6 else "streams from DRAM every pass"))}
 
     out = None
     if rank == 0:
@@ -308,7 +315,7 @@ def run_ours(a, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "atoms": a.atoms, "rules": a.rules,
+            "config": {"workload": workload(a), "atoms": a.atoms, "rules": a.rules,
                        "conflict_budget_per_step": a.conflicts, "n_vars": st["n_vars"],
                        "n_nogoods": st["n_nogoods"], "n_literals": st["n_literals"],
                        "store_bytes": st["store_bytes"], "l2": "flushed between steps (1 GiB write)",
