@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--atoms", type=int, default=100_000)
     ap.add_argument("--rules", type=int, default=400_000)
     ap.add_argument("--conflicts", type=int, default=200, help="conflict budget per step")
+    ap.add_argument("--view", type=int, default=0, help="sweep view layout: 0 auto, 1 plain, 2 packed, 3 bytes")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample length")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -151,7 +152,7 @@ def _traffic(kernel_src_sha, checks_per_launch, atoms, rules):
 
 def _src_sha():
     h = hashlib.sha256()
-    for f in ("solver.cu", "device.cuh", "store.cpp", "store.h"):
+    for f in ("solver.cuh", "solve.cu", "sweep.cu", "device.cuh", "store.cpp", "store.h", "api.cpp"):
         h.update(open(os.path.join(ROOT, "paper_1909_01786_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -197,7 +198,7 @@ def run_ours(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     prog = _program(a)
-    P = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000)
+    P = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000, view_mode=a.view)
     words = max((prog.n_atoms + 63) // 64, 1)
     d_models = torch.zeros(words, dtype=torch.int64, device=dev)
     d_result = torch.zeros(4, dtype=torch.int64, device=dev)
@@ -297,7 +298,7 @@ def run_ours(a, rank, world, local_rank):
             for _ in range(n_e2e):
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
-                Q = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000)
+                Q = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000, view_mode=a.view)
                 Q.solve(1, cap=1)
                 s = Q.stats()
                 Q.close()
@@ -319,6 +320,7 @@ def run_ours(a, rank, world, local_rank):
                        "conflict_budget_per_step": a.conflicts, "n_vars": st["n_vars"],
                        "n_nogoods": st["n_nogoods"], "n_literals": st["n_literals"],
                        "store_bytes": st["store_bytes"], "l2": "flushed between steps (1 GiB write)",
+                       "view": {1: "plain 2-bit", 2: "packed 2-bit", 3: "bytes"}.get(st["view_mode"]),
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": a.steps,
             "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "batched": batched,
@@ -444,12 +446,13 @@ def run_sweeps(a):
     import torch
     from paper_1909_01786_gb300 import aspgpu
     prog = _program(a)
-    P = aspgpu.Program(prog)
+    P = aspgpu.Program(prog, view_mode=a.view)
     P.propagate(np.zeros(P.n_vars, np.int8))
     for _ in range(3):
         P.sweep(a.sweep_only)
     torch.cuda.synchronize()
-    print(json.dumps({"sweeps": a.sweep_only, "store_bytes": P.stats()["store_bytes"]}))
+    st = P.stats()
+    print(json.dumps({"sweeps": a.sweep_only, "store_bytes": st["store_bytes"], "view_mode": st["view_mode"]}))
 
 
 def main():

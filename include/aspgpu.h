@@ -56,6 +56,18 @@ extern "C" {
 #define ASP_HEUR_ACTIVITY 1   /* occurrence count plus activity bumped by conflicts */
 #define ASP_HEUR_LEARNED 2    /* log1p(head occurrences) + log sigmoid(MLP logit) (not in the paper) */
 
+/* Shared-memory assignment view of each CTA during the propagate-and-check
+ * sweep (Section 4.1; the layout is this implementation's, not the paper's).
+ * PLAIN: 2 bits per variable, nogood literals name variables, variables
+ * outside the view are read from global memory.  PACKED: 2 bits per
+ * variable, every variable the CTA's nogoods name is in the view, and the
+ * sweep reads a copy of the static store whose literals name view entries.
+ * BYTES: as PACKED with one byte per variable. */
+#define ASP_VIEW_AUTO 0       /* widest that fits: BYTES, PACKED, PLAIN */
+#define ASP_VIEW_PLAIN 1
+#define ASP_VIEW_PACKED 2
+#define ASP_VIEW_BYTES 3
+
 #define ASP_MLP_FEATURES 16   /* inputs of the learned heuristic per candidate rule */
 #define ASP_MLP_PARAMS 1153   /* W1[64][16], b1[64], w2[64], b2 */
 
@@ -81,6 +93,10 @@ typedef struct {
     const float *mlp_weights;
     /* record up to this many decisions per solve for asp_trace; 0 = none */
     int64_t trace_capacity;
+    /* ASP_VIEW_*: the widest view allowed (a wider one than fits in shared
+       memory falls back to the next narrower); 0 = ASP_VIEW_AUTO */
+    int32_t view_mode;
+    int32_t reserved0;
 } asp_options;
 
 typedef struct {
@@ -96,6 +112,8 @@ typedef struct {
     int64_t ns_total, ns_sweep, ns_analysis, ns_decision, ns_stability; /* device time */
     int64_t ns_buckets, ns_learned, ns_barrier; /* CTA 0: static buckets, long and learned
                                                    nogoods, waiting at phase barriers */
+    int64_t view_mode, batch_view_mode;         /* ASP_VIEW_* chosen for asp_solve and for
+                                                   asp_solve_batch */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */

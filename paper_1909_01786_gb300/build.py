@@ -13,7 +13,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libaspgpu.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["solver.cu", "noalloc.cu", "mlp.cu", "api.cpp", "store.cpp"]
+SOURCES = ["solve.cu", "batch.cu", "sweep.cu", "noalloc.cu", "mlp.cu", "api.cpp", "store.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -108,6 +108,79 @@ static T *upload(asp_prog *p, const std::vector<T> &v, int &rc)
 // shared memory for the heuristic's bf16 weights, after the view
 constexpr size_t MLP_SMEM_BYTES = ((2 * MLP_PARAMS + 15) / 16) * 16;
 
+// The buckets' literals rewritten for the view of the CTA that owns each
+// nogood: (entry << 2) | (3 if false), with entry = v for an atom and
+// aux_base + (v - alo[c]) for an auxiliary variable of the CTA's slice.
+// False if some literal names a variable outside the owner's view.
+static bool translate_buckets(const Dev &D, const HostStore &H, const std::vector<uint32_t> &boff,
+                              uint32_t G, const std::vector<uint32_t> &alo, const std::vector<uint32_t> &an,
+                              uint32_t aux_base, std::vector<uint32_t> &out)
+{
+    const uint32_t G1 = G + 1u;
+    out.assign((size_t)D.bk_base[BUCKET_MAX] + (size_t)BUCKET_MAX * D.bk_n[BUCKET_MAX], 0u);
+    for (int L = 2; L <= BUCKET_MAX; L++) {
+        const std::vector<uint32_t> &rows = H.bucket_rows[L];
+        const size_t n = D.bk_n[L];
+        for (uint32_t c = 0; c < G; c++) {
+            for (uint32_t k = boff[L * G1 + c]; k < boff[L * G1 + c + 1]; k++) {
+                for (int q = 0; q < L; q++) {
+                    const uint32_t l = rows[(size_t)k * L + q], v = l >> 1;
+                    uint32_t e;
+                    if (v < D.na) e = v;
+                    else if (v - alo[c] < an[c]) e = aux_base + (v - alo[c]);
+                    else return false;
+                    out[D.bk_base[L] + (size_t)q * n + k] = (e << 2) | ((l & 1u) ? 3u : 0u);
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// View of G CTAs with auxiliary slices (alo, an) in `budget` bytes of
+// shared memory after `base` bytes: the widest mode allowed by the options
+// that fits (and whose literals translate), else PLAIN with atoms read from
+// global memory if they do not fit either.  Sets view_mode, view_atoms,
+// view_words and vlits; may clear an[] (PLAIN without auxiliary slice).
+static int choose_view(asp_prog *p, const HostStore &H, Dev &D, const std::vector<uint32_t> &boff,
+                       const std::vector<uint32_t> &alo, std::vector<uint32_t> &an, size_t base, size_t budget)
+{
+    uint32_t max_an = 0;
+    for (uint32_t x : an) max_an = std::max(max_an, x);
+    const uint32_t want = p->opt.view_mode > 0 ? (uint32_t)p->opt.view_mode : (uint32_t)VIEW_BYTES;
+    const size_t aux_base = ((size_t)D.na + 15u) / 16u * 16u;
+    const size_t bytes_words = (aux_base + max_an + 3u) / 4u;
+    const size_t packed_words = aux_base / 16u + (max_an + 15u) / 16u;
+    uint32_t mode = VIEW_PLAIN;
+    if (want >= VIEW_BYTES && base + 4 * bytes_words <= budget) mode = VIEW_BYTES;
+    else if (want >= VIEW_PACKED && base + 4 * packed_words <= budget) mode = VIEW_PACKED;
+    std::vector<uint32_t> vl;
+    if (mode != VIEW_PLAIN && !translate_buckets(D, H, boff, D.G, alo, an, (uint32_t)aux_base, vl)) mode = VIEW_PLAIN;
+    D.view_mode = mode;
+    D.vlits = nullptr;
+    if (mode != VIEW_PLAIN) {
+        D.view_atoms = D.na;
+        D.view_words = (uint32_t)(mode == VIEW_BYTES ? bytes_words : packed_words);
+        int rc = ASP_OK;
+        D.vlits = upload(p, vl, rc);
+        return rc;
+    }
+    size_t atoms_words = (D.na + 15u) / 16u;
+    size_t aux_words = (max_an + 15u) / 16u;
+    D.view_atoms = D.na;
+    if (base + 4 * (atoms_words + aux_words) > budget) {
+        // too big for shared memory: keep the auxiliary slice, read atoms globally
+        D.view_atoms = 0;
+        atoms_words = 0;
+        if (base + 4 * aux_words > budget) {
+            std::fill(an.begin(), an.end(), 0u);
+            aux_words = 0;
+        }
+    }
+    D.view_words = (uint32_t)(atoms_words + aux_words);
+    return ASP_OK;
+}
+
 // Grid size, the static partition of the buckets over the CTAs along groups
 // (an atom with its rules; a constraint), each CTA's slice of auxiliary
 // variables kept in shared memory, and the shared-memory layout.
@@ -155,29 +228,15 @@ static int plan_grid(asp_prog *p, const HostStore &H)
     for (uint32_t j = 0; j < D.J; j++) first[H.rule_head[j] + 1]++;
     for (uint32_t a = 0; a < D.na; a++) first[a + 1] += first[a];
     std::vector<uint32_t> alo(g), an(g);
-    uint32_t max_an = 0;
     for (int i = 0; i < g; i++) {
         uint32_t a0 = std::min(glo[i], D.na), a1 = std::min(glo[i + 1], D.na);
         uint32_t j0 = first[a0], j1 = first[a1];
         alo[i] = D.na + 3 * j0;
         an[i] = 3 * (j1 - j0);
-        max_an = std::max(max_an, an[i]);
     }
-    size_t atoms_words = (D.na + 15u) / 16u;
-    size_t aux_words = (max_an + 15u) / 16u;
-    D.view_atoms = D.na;
-    if (base_smem + 4 * (atoms_words + aux_words) > max_smem) {
-        // too big for shared memory: keep the auxiliary slice, read atoms globally
-        D.view_atoms = 0;
-        atoms_words = 0;
-        if (base_smem + 4 * aux_words > max_smem) {
-            std::fill(an.begin(), an.end(), 0u);
-            aux_words = 0;
-        }
-    }
-    D.view_words = (uint32_t)(atoms_words + aux_words);
+    int rc = choose_view(p, H, D, boff, alo, an, base_smem, max_smem);
+    if (rc != ASP_OK) return rc;
     p->smem = base_smem + 4 * D.view_words;
-    int rc = ASP_OK;
     D.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D.cta_auxn = upload(p, an, rc);
@@ -201,16 +260,9 @@ static int plan_batch(asp_prog *p, const HostStore &H)
     alo[0] = D1.na;
     an[0] = 3 * D1.J;
     const size_t base = 8ull * D1.WW + 8ull * 32 + 4ull * 16 + MLP_SMEM_BYTES;
-    size_t aw = (D1.na + 15u) / 16u, xw = (an[0] + 15u) / 16u;
-    D1.view_atoms = D1.na;
-    if (base + 4 * (aw + xw) > BATCH_SMEM_BUDGET) {
-        D1.view_atoms = 0;
-        aw = 0;
-        if (base + 4 * xw > BATCH_SMEM_BUDGET) { an[0] = 0; xw = 0; }
-    }
-    D1.view_words = (uint32_t)(aw + xw);
     D1.G = 1;
-    int rc = ASP_OK;
+    int rc = choose_view(p, H, D1, boff, alo, an, base, BATCH_SMEM_BUDGET);
+    if (rc != ASP_OK) return rc;
     D1.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D1.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D1.cta_auxn = upload(p, an, rc);
@@ -436,6 +488,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.ns_total = (int64_t)s.ns_total; o.ns_sweep = (int64_t)s.ns_sweep; o.ns_analysis = (int64_t)s.ns_analysis;
     o.ns_decision = (int64_t)s.ns_decision; o.ns_stability = (int64_t)s.ns_stab;
     o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
+    o.view_mode = D.view_mode; o.batch_view_mode = p->D1.view_mode;
 }
 
 extern "C" {

@@ -1,0 +1,66 @@
+// Batched solving: many programs in one launch, one CTA per program
+// (device code in solver.cuh).
+#include "solver.cuh"
+
+namespace aspgpu {
+
+// Batched solving: each CTA takes programs from a queue (the host orders it
+// largest first) and solves each alone, with the whole program's assignment
+// view in its shared memory and __syncthreads as the phase barrier.
+__global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
+                                                       unsigned int *queue)
+{
+    extern __shared__ unsigned long long smem_raw[];
+    __shared__ Dev sD;
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t i = atomicAdd(queue, 1u);
+            s_item = i < n ? __ldg(order + i) : 0xFFFFFFFFu;
+            if (s_item != 0xFFFFFFFFu) sD = devs[s_item];
+        }
+        __syncthreads();
+        if (s_item == 0xFFFFFFFFu) break;
+        const Dev &D = sD;
+        // reset this program's search state
+        for (uint32_t w = threadIdx.x; w <= D.asg_words; w += blockDim.x) D.asg[w] = 0u;
+        for (uint32_t v = threadIdx.x; v < D.nv; v += blockDim.x) D.dl[v] = 0;
+        for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) D.act[j] = 0u;
+        if (threadIdx.x == 0) {
+            Ctl c;
+            memset(&c, 0, sizeof(c));
+            c.op = OP_INIT;
+            c.cdl = 1;
+            c.lfill = D.lits_static;
+            D.ctl[0] = c;
+            memset(&c, 0, sizeof(c));
+            D.ctl[1] = c;
+            Acc a;
+            a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+            for (int i = 0; i < 4; i++) D.acc[i] = a;
+            memset(D.stats, 0, sizeof(DevStats));
+            memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check
+        }
+        __syncthreads();
+        const Smem S = make_smem(D, smem_raw);
+        const View V = make_view(D, S.misc + 16, 0);
+        solver_loop<true>(D, S, V, threadIdx.x, blockDim.x, true, threadIdx.x == 0, 0);
+        __syncthreads();
+    }
+}
+
+cudaError_t batch_configure(size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem);
+}
+
+cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
+                         size_t smem, cudaStream_t st)
+{
+    batch_kernel<<<grid, 256, smem, st>>>(devs, order, n, queue);
+    return cudaGetLastError();
+}
+
+}  // namespace aspgpu

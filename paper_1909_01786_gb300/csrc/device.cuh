@@ -34,6 +34,9 @@ enum Op : uint32_t {
 
 enum Mode : uint32_t { MODE_SOLVE = 0, MODE_PROPAGATE = 1 };
 
+// Shared-memory view of a CTA (values ASP_VIEW_PLAIN/PACKED/BYTES)
+enum ViewMode : uint32_t { VIEW_PLAIN = 1, VIEW_PACKED = 2, VIEW_BYTES = 3 };
+
 constexpr unsigned long long NO_KEY = ~0ull;
 
 // learned heuristic: 16 features -> 64 hidden (ReLU) -> 1, parameters
@@ -92,10 +95,14 @@ struct Dev {
     // cta_boff[L*(G+1)+g+1]) of bucket L, and keeps in shared memory the
     // atoms [0, view_atoms) and the auxiliary variables
     // [cta_auxlo, cta_auxlo + cta_auxn) those nogoods refer to
-    uint32_t G, view_atoms, view_words, pad2;
+    uint32_t G, view_atoms, view_words, view_mode;
     const uint32_t *cta_boff;    // [16 * (G+1)]
     const uint32_t *cta_auxlo;   // [G]
     const uint32_t *cta_auxn;    // [G]
+    // view_mode PACKED or BYTES: the buckets again (same offsets), each
+    // literal rewritten for its owner CTA as (view entry << 2) | xmask with
+    // xmask = 3 for a false literal, 0 for a true one
+    const uint32_t *vlits;
     long long max_models, models_cap, conflict_budget, time_budget_ns;
     unsigned long long static_checks;    // literals of the buckets (read every sweep)
     uint32_t *lits;                      // buckets | long | units | learned

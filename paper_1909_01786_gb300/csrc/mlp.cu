@@ -3,7 +3,7 @@
 // momentum on binary cross-entropy, in one CTA.  One lane holds one sample;
 // gradients are reduced across the warp with shuffles and summed into shared
 // memory.  The solver evaluates the trained network with bf16 weights and
-// fp32 accumulation (solver.cu, mlp_score).
+// fp32 accumulation (solver.cuh, mlp_score).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

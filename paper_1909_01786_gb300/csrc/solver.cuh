@@ -21,6 +21,7 @@
 // can resolve within one sweep; other CTAs see the claim after the next
 // barrier.  Long and learned nogoods are classified by one warp each (ballot
 // and popc over lanes), against the global codes.
+#pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -138,12 +139,14 @@ __device__ __forceinline__ uint32_t ng_len(const Dev &D, uint32_t id)
 
 // ---------------------------------------------------------------- views
 
-// The CTA's 2-bit view (0 unassigned, 1 true, 2 false) of the atoms
-// [0, na_v) and of the auxiliary variables [auxlo, auxlo + auxn), which
-// follow the atoms at entry aux_base (a multiple of 16).
+// The CTA's view (0 unassigned, 1 true, 2 false; 2 bits or one byte per
+// entry) of the atoms [0, na_v) and of the auxiliary variables
+// [auxlo, auxlo + auxn), which follow the atoms at entry aux_base (a
+// multiple of 16).
 struct View {
     volatile uint32_t *w;
     uint32_t na_v, aux_base, auxlo, auxn;
+    bool bytes;
 
     // entry of v in the view, or 0xFFFFFFFF if v is not in it
     __device__ __forceinline__ uint32_t index(uint32_t v) const
@@ -152,28 +155,50 @@ struct View {
         uint32_t k = v - auxlo;
         return k < auxn ? aux_base + k : 0xFFFFFFFFu;
     }
+    // variable of entry i
+    __device__ __forceinline__ uint32_t var(uint32_t i) const { return i < aux_base ? i : i - aux_base + auxlo; }
+    __device__ __forceinline__ uint32_t get(uint32_t i) const
+    {
+        if (bytes) return reinterpret_cast<volatile const uint8_t *>(w)[i];
+        return (w[i >> 4] >> (2u * (i & 15u))) & 3u;
+    }
+    // set entry i to val; true if it was unassigned
+    __device__ __forceinline__ bool put(uint32_t i, uint32_t val) const
+    {
+        if (bytes) {
+            volatile uint8_t *b = reinterpret_cast<volatile uint8_t *>(w);
+            const uint32_t old = b[i];
+            b[i] = (uint8_t)val;
+            return old == 0u;
+        }
+        uint32_t sh = 2u * (i & 15u);
+        uint32_t old = atomicOr((uint32_t *)(w + (i >> 4)), val << sh);
+        return ((old >> sh) & 3u) == 0u;
+    }
+    __device__ __forceinline__ void clear(uint32_t i) const
+    {
+        if (bytes) reinterpret_cast<volatile uint8_t *>(w)[i] = 0;
+        else atomicAnd((uint32_t *)(w + (i >> 4)), ~(3u << (2u * (i & 15u))));
+    }
 };
 
 __device__ __forceinline__ uint32_t view_val(const Dev &D, const View &V, uint32_t v, uint32_t fresh_cur)
 {
     uint32_t i = V.index(v);
-    if (i != 0xFFFFFFFFu) return (V.w[i >> 4] >> (2u * (i & 15u))) & 3u;
+    if (i != 0xFFFFFFFFu) return V.get(i);
     return global_val(D, v, fresh_cur);
 }
 
 __device__ __forceinline__ bool view_set(const View &V, uint32_t v, uint32_t val)
 {
     uint32_t i = V.index(v);
-    if (i == 0xFFFFFFFFu) return false;
-    uint32_t sh = 2u * (i & 15u);
-    uint32_t old = atomicOr((uint32_t *)(V.w + (i >> 4)), val << sh);
-    return ((old >> sh) & 3u) == 0u;
+    return i != 0xFFFFFFFFu && V.put(i, val);
 }
 
 __device__ __forceinline__ void view_clear(const View &V, uint32_t v)
 {
     uint32_t i = V.index(v);
-    if (i != 0xFFFFFFFFu) atomicAnd((uint32_t *)(V.w + (i >> 4)), ~(3u << (2u * (i & 15u))));
+    if (i != 0xFFFFFFFFu) V.clear(i);
 }
 
 // 2-bit effective values of the 8 variables of one global code word
@@ -185,10 +210,49 @@ __device__ __forceinline__ uint32_t pack8(uint32_t word, uint32_t fresh_cur)
     return m;
 }
 
+// effective values of the 4 variables at nibbles sh..sh+3 of code words
+// (a, b), one per byte
+__device__ __forceinline__ uint32_t bytes4(uint32_t a, uint32_t b, uint32_t sh, uint32_t fresh_cur)
+{
+    const uint32_t x = (uint32_t)((((unsigned long long)b << 32) | a) >> (4u * sh));
+    uint32_t m = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 4u; q++) m |= eff_val((x >> (4u * q)) & 0xFu, fresh_cur) << (8u * q);
+    return m;
+}
+
+// Byte view: one view word holds 4 variables (half a global code word).
+__device__ __forceinline__ void view_reload_bytes(const Dev &D, const View &V, uint32_t fresh_cur)
+{
+    const uint32_t wa = (V.na_v + 3u) >> 2, wx = (V.auxn + 3u) >> 2;
+    for (uint32_t k = threadIdx.x; k < wa; k += blockDim.x) {
+        const uint32_t v0 = 4u * k;
+        uint32_t m = bytes4(__ldcg(D.asg + (v0 >> 3)), 0u, v0 & 7u, fresh_cur);
+        const uint32_t valid = V.na_v - v0;
+        if (valid < 4u) m &= (1u << (8u * valid)) - 1u;
+        V.w[k] = m;
+    }
+    for (uint32_t k = wa + threadIdx.x; k < V.aux_base / 4u; k += blockDim.x) V.w[k] = 0u;
+    for (uint32_t k = threadIdx.x; k < wx; k += blockDim.x) {
+        const uint32_t v0 = V.auxlo + 4u * k, w0 = v0 >> 3;
+        const uint32_t a = __ldcg(D.asg + w0);
+        const uint32_t b = w0 + 1u < D.asg_words ? __ldcg(D.asg + w0 + 1u) : 0u;
+        uint32_t m = bytes4(a, b, v0 & 7u, fresh_cur);
+        const uint32_t valid = V.auxn - 4u * k;
+        if (valid < 4u) m &= (1u << (8u * valid)) - 1u;
+        V.w[V.aux_base / 4u + k] = m;
+    }
+}
+
 // Rebuild the whole view from the global codes (fresh claims read as
-// unassigned); one view word holds 16 variables = two global code words.
+// unassigned); one 2-bit view word holds 16 variables = two global code
+// words.
 __device__ __forceinline__ void view_reload(const Dev &D, const View &V, uint32_t fresh_cur)
 {
+    if (V.bytes) {
+        view_reload_bytes(D, V, fresh_cur);
+        return;
+    }
     const uint32_t wa = (V.na_v + 15u) >> 4, wx = (V.auxn + 15u) >> 4;
     for (uint32_t k = threadIdx.x; k < wa; k += blockDim.x) {
         uint32_t lo = __ldcg(D.asg + 2u * k), hi = 2u * k + 1u < D.asg_words ? __ldcg(D.asg + 2u * k + 1u) : 0u;
@@ -293,10 +357,10 @@ __device__ __forceinline__ uint32_t lit_val(const SweepCtx &X, uint32_t l)
     return X.use_view ? view_val(*X.D, X.V, l >> 1, X.fresh) : global_val(*X.D, l >> 1, X.fresh);
 }
 
-// Dependency bitmap of x from the other literals of one lane's nogood (lit),
-// OR over those with level > 1 (Section 4.2, mk_dl_bitmap).
+// Dependency bitmap of x from the other variables of one lane's nogood
+// (var), OR over those with level > 1 (Section 4.2, mk_dl_bitmap).
 template <int L>
-__device__ __forceinline__ void lane_deps(const SweepCtx &X, const uint32_t (&lit)[L], uint32_t x)
+__device__ __forceinline__ void lane_deps(const SweepCtx &X, const uint32_t (&var)[L], uint32_t x)
 {
     const Dev &D = *X.D;
     const uint32_t nw = deps_words(D, X.cdl);
@@ -304,14 +368,14 @@ __device__ __forceinline__ void lane_deps(const SweepCtx &X, const uint32_t (&li
     int32_t Lu[L];
 #pragma unroll
     for (int q = 0; q < L; q++) {
-        uint32_t u = lit[q] >> 1;
+        uint32_t u = var[q];
         Lu[q] = (u == x) ? 0 : (u == X.dec_v) ? (int32_t)X.cdl : __ldcg(D.dl + u);
     }
     for (uint32_t w = 0; w < nw; w++) {
         unsigned long long acc = 0;
 #pragma unroll
         for (int q = 0; q < L; q++) {
-            uint32_t u = lit[q] >> 1;
+            uint32_t u = var[q];
             if (Lu[q] > 1 && w < deps_words(D, (uint32_t)Lu[q]))
                 acc |= (u == X.dec_v) ? (w == (dbit >> 6) ? (1ull << (dbit & 63u)) : 0ull)
                                       : __ldcg(D.deps + (size_t)u * D.WW + w);
@@ -368,7 +432,12 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
             if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
             if (r != 0) continue;
             record_claim(X, x, id);
-            if (X.cdl > 1u) lane_deps<L>(X, lit[t], x);
+            if (X.cdl > 1u) {
+                uint32_t var[L];
+#pragma unroll
+                for (int q = 0; q < L; q++) var[q] = lit[t][q] >> 1;
+                lane_deps<L>(X, var, x);
+            }
             if (X.use_view) {
                 __threadfence_block();
                 pub |= view_set(X.V, x, valbit);
@@ -378,9 +447,112 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
     }
 }
 
+// Contribution of one translated literal (entry << 2 | xmask) to its
+// nogood's count: t = value ^ xmask is 1 if the literal holds, 2 if its
+// complement holds, 0 or 3 if unassigned; the byte of 0x01100001 at t is
+// 0, 16 or 1.  Over at most 15 literals the low byte of the sum is
+// >= 16: satisfied; 0: violated; 1: unit; 2..15: two or more unassigned.
+template <bool BYTES>
+__device__ __forceinline__ uint32_t tlit_val(const View &V, uint32_t tl)
+{
+    const uint32_t i = tl >> 2;
+    if (BYTES) return reinterpret_cast<volatile const uint8_t *>(V.w)[i];
+    return V.w[i >> 4] >> (2u * (i & 15u));
+}
+template <bool BYTES>
+__device__ __forceinline__ uint32_t tlit_count(const View &V, uint32_t tl)
+{
+    return __byte_perm(0x01100001u, 0u, (tlit_val<BYTES>(V, tl) ^ tl) & 3u);
+}
+
+// bucket_tasks over the translated copy of the store (view modes PACKED
+// and BYTES): every literal is in the view, one shared-memory load and
+// three integer operations classify it.  Lanes past the end of the range
+// load the range's last nogood and drop the result.
+template <int L, int U, bool BYTES>
+__device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0, uint32_t k1)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t *base = D.vlits + D.bk_base[L];
+    const uint32_t n = D.bk_n[L];
+    uint32_t lit[U][L];
+#pragma unroll
+    for (int t = 0; t < U; t++) {
+        const uint32_t k = min(k0 + (uint32_t)t * 32u + lane, k1 - 1u);
+#pragma unroll
+        for (int q = 0; q < L; q++) lit[t][q] = __ldg(base + (size_t)q * n + k);
+    }
+    for (int pass = 0; pass < 8; pass++) {
+        uint32_t cnt[U];
+#pragma unroll
+        for (int t = 0; t < U; t++) {
+            cnt[t] = 0u;
+#pragma unroll
+            for (int q = 0; q < L; q++) cnt[t] += tlit_count<BYTES>(X.V, lit[t][q]);
+        }
+        bool pub = false;
+#pragma unroll
+        for (int t = 0; t < U; t++) {
+            const uint32_t k = k0 + (uint32_t)t * 32u + lane;
+            if (k >= k1 || (cnt[t] & 0xFFu) > 1u) continue;
+            const uint32_t id = bucket_nogood_id((uint32_t)L, k);
+            // violated or unit: classify again from the current view (a
+            // claim of this CTA may have changed it since the count)
+            bool sat = false;
+            uint32_t n_un = 0, ul = 0;
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+                const uint32_t tv = (tlit_val<BYTES>(X.V, lit[t][q]) ^ lit[t][q]) & 3u;
+                sat |= tv == 2u;
+                if (tv == 0u || tv == 3u) { n_un++; ul = lit[t][q]; }
+            }
+            if (sat || n_un > 1u) continue;
+            if (n_un == 0u) { report_conflict(X, id, (uint32_t)L); continue; }
+            if (!X.do_claim) { atomicAdd(&X.acc->flag, 1u); continue; }
+            const uint32_t e = ul >> 2, x = X.V.var(e), valbit = (ul & 1u) ? V_T : V_F;
+            const int r = claim_var(D.asg, x, valbit, X.fresh);
+            if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
+            if (r != 0) continue;
+            record_claim(X, x, id);
+            if (X.cdl > 1u) {
+                uint32_t var[L];
+#pragma unroll
+                for (int q = 0; q < L; q++) var[q] = X.V.var(lit[t][q] >> 2);
+                lane_deps<L>(X, var, x);
+            }
+            __threadfence_block();
+            X.V.put(e, valbit);
+            pub = true;
+        }
+        if (!X.do_claim || !__any_sync(FULL_MASK, pub)) break;
+    }
+}
+
 // Groups of 32 nogoods per unit of work, by bucket length: about 16 literal
 // loads in flight per lane.
 __host__ __device__ constexpr uint32_t unit_groups(uint32_t L) { return L <= 2u ? 8u : L <= 4u ? 4u : L <= 8u ? 2u : 1u; }
+
+template <bool BYTES>
+__device__ __forceinline__ void run_unit_view(const SweepCtx &X, uint32_t L, uint32_t k0, uint32_t k1)
+{
+    switch (L) {
+    case 2: bucket_tasks_view<2, unit_groups(2), BYTES>(X, k0, k1); break;
+    case 3: bucket_tasks_view<3, unit_groups(3), BYTES>(X, k0, k1); break;
+    case 4: bucket_tasks_view<4, unit_groups(4), BYTES>(X, k0, k1); break;
+    case 5: bucket_tasks_view<5, unit_groups(5), BYTES>(X, k0, k1); break;
+    case 6: bucket_tasks_view<6, unit_groups(6), BYTES>(X, k0, k1); break;
+    case 7: bucket_tasks_view<7, unit_groups(7), BYTES>(X, k0, k1); break;
+    case 8: bucket_tasks_view<8, unit_groups(8), BYTES>(X, k0, k1); break;
+    case 9: bucket_tasks_view<9, unit_groups(9), BYTES>(X, k0, k1); break;
+    case 10: bucket_tasks_view<10, unit_groups(10), BYTES>(X, k0, k1); break;
+    case 11: bucket_tasks_view<11, unit_groups(11), BYTES>(X, k0, k1); break;
+    case 12: bucket_tasks_view<12, unit_groups(12), BYTES>(X, k0, k1); break;
+    case 13: bucket_tasks_view<13, unit_groups(13), BYTES>(X, k0, k1); break;
+    case 14: bucket_tasks_view<14, unit_groups(14), BYTES>(X, k0, k1); break;
+    default: bucket_tasks_view<15, unit_groups(15), BYTES>(X, k0, k1); break;
+    }
+}
 
 __device__ __forceinline__ void run_unit(const SweepCtx &X, uint32_t L, uint32_t k0, uint32_t k1)
 {
@@ -512,12 +684,16 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
         if (lane == 0) u = atomicAdd(&s_unit, 1u);
         u = __shfl_sync(FULL_MASK, u, 0);
         if (u >= units) break;
-        uint32_t L = 2;
+        uint32_t L = 2, first = 0;
 #pragma unroll
-        for (uint32_t q = 3; q <= (uint32_t)BUCKET_MAX; q++) if (u >= ubase[q]) L = q;
+        for (uint32_t q = 3; q <= (uint32_t)BUCKET_MAX; q++)
+            if (u >= ubase[q]) { L = q; first = ubase[q]; }
         const uint32_t b0 = __ldg(D.cta_boff + L * G1 + X.cta);
         const uint32_t b1 = __ldg(D.cta_boff + L * G1 + X.cta + 1u);
-        run_unit(X, L, b0 + (u - ubase[L]) * unit_groups(L) * 32u, b1);
+        const uint32_t k0 = b0 + (u - first) * unit_groups(L) * 32u;
+        if (D.view_mode == VIEW_BYTES) run_unit_view<true>(X, L, k0, b1);
+        else if (D.view_mode == VIEW_PACKED) run_unit_view<false>(X, L, k0, b1);
+        else run_unit(X, L, k0, b1);
     }
     unsigned long long checks = 0;
     const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
@@ -780,6 +956,7 @@ __device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase, uint32_
     V.w = vbase;
     V.na_v = D.view_atoms;
     V.aux_base = ((D.view_atoms + 15u) >> 4) << 4;
+    V.bytes = D.view_mode == VIEW_BYTES;
     V.auxlo = __ldg(D.cta_auxlo + cta);
     V.auxn = __ldg(D.cta_auxn + cta);
     return V;
@@ -851,12 +1028,20 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         const Acc A = sA;
         if (C.op == OP_DONE) break;
         Acc *acc = D.acc + (k & 3u);
-        Ctl N = C;
+        // the next control block, written by the leader only (kept in
+        // shared memory rather than in every thread's registers)
+        __shared__ Ctl sN;
+        Ctl &N = sN;
+        if (leader) N = C;
         int kind = 0;   // 0 sweep, 1 analysis, 2 decision, 3 stability
         const uint32_t tend = C.tb + A.nclaim;
         const uint32_t fresh_cur = 4u << (C.round & 1u);
         const uint32_t fresh_prev = 4u << ((C.round + 1u) & 1u);
 
+        // the propagate-and-check sweep of ROUND and APPLY runs after the
+        // switch (one copy of its code)
+        bool sw = false;
+        uint32_t sw_cdl = 0, sw_tbase = 0, sw_dec = 0xFFFFFFFFu;
         switch (C.op) {
         case OP_INIT: {
             SweepCtx X{&D, V, fresh_cur, 1u, tend, acc, true, false, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
@@ -950,8 +1135,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 }
             }
             __syncthreads();
-            SweepCtx X{&D, V, fresh_cur, C.cdl, tend, acc, true, true, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
-            sweep(X, C.n_learned);
+            sw = true; sw_cdl = C.cdl; sw_tbase = tend;
             if (leader) {
                 N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1;
                 atomicAdd(&D.stats->rounds, 1ull);
@@ -999,8 +1183,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             if (threadIdx.x == 0) view_set(V, bv, V_T);
             __syncthreads();
-            SweepCtx X{&D, V, fresh_cur, L, tend + 1u, acc, true, true, bv, cta, rank >> 5, size >> 5};
-            sweep(X, C.n_learned);
+            sw = true; sw_cdl = L; sw_tbase = tend + 1u; sw_dec = bv;
             if (leader) {
                 N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
                 N.clean = 0;
@@ -1185,6 +1368,10 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             if (leader) { N.op = OP_DONE; N.err = -6; }
             break;
         }
+        if (sw) {
+            SweepCtx X{&D, V, fresh_cur, sw_cdl, sw_tbase, acc, true, true, sw_dec, cta, rank >> 5, size >> 5};
+            sweep(X, C.n_learned);
+        }
 
         if (leader) {
             if (D.mode == MODE_SOLVE && N.op != OP_DONE) {
@@ -1225,126 +1412,9 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     }
 }
 
-__global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
-{
-    extern __shared__ unsigned long long smem_raw[];
-    const Smem S = make_smem(D, smem_raw);
-    const View V = make_view(D, S.misc + 16, blockIdx.x);
-    solver_loop<false>(D, S, V, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, blockIdx.x == 0,
-                       blockIdx.x == 0 && threadIdx.x == 0, blockIdx.x);
-}
-
-// Batched solving: each CTA takes programs from a queue (the host orders it
-// largest first) and solves each alone, with the whole program's assignment
-// view in its shared memory and __syncthreads as the phase barrier.
-__global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
-                                                       unsigned int *queue)
-{
-    extern __shared__ unsigned long long smem_raw[];
-    __shared__ Dev sD;
-    __shared__ uint32_t s_item;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            uint32_t i = atomicAdd(queue, 1u);
-            s_item = i < n ? __ldg(order + i) : 0xFFFFFFFFu;
-            if (s_item != 0xFFFFFFFFu) sD = devs[s_item];
-        }
-        __syncthreads();
-        if (s_item == 0xFFFFFFFFu) break;
-        const Dev &D = sD;
-        // reset this program's search state
-        for (uint32_t w = threadIdx.x; w <= D.asg_words; w += blockDim.x) D.asg[w] = 0u;
-        for (uint32_t v = threadIdx.x; v < D.nv; v += blockDim.x) D.dl[v] = 0;
-        for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) D.act[j] = 0u;
-        if (threadIdx.x == 0) {
-            Ctl c;
-            memset(&c, 0, sizeof(c));
-            c.op = OP_INIT;
-            c.cdl = 1;
-            c.lfill = D.lits_static;
-            D.ctl[0] = c;
-            memset(&c, 0, sizeof(c));
-            D.ctl[1] = c;
-            Acc a;
-            a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
-            for (int i = 0; i < 4; i++) D.acc[i] = a;
-            memset(D.stats, 0, sizeof(DevStats));
-            memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check
-        }
-        __syncthreads();
-        const Smem S = make_smem(D, smem_raw);
-        const View V = make_view(D, S.misc + 16, 0);
-        solver_loop<true>(D, S, V, threadIdx.x, blockDim.x, true, threadIdx.x == 0, 0);
-        __syncthreads();
-    }
-}
-
-// One sweep over the static store without claiming (timing the sweep kernel
-// in isolation): counts unit nogoods in acc->flag, conflicts in acc->ckey.
-// Same partition, views and classification as the solver's sweep.
-__global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc, uint32_t passes)
-{
-    extern __shared__ unsigned long long smem_raw[];
-    uint32_t *vbase = reinterpret_cast<uint32_t *>(smem_raw + D.WW + 32) + 16;
-    const View V = make_view(D, vbase, blockIdx.x);
-    view_reload(D, V, 0u);
-    __syncthreads();
-    for (uint32_t pass = 1; pass < passes; pass++) {
-        SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
-                   (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
-        sweep(X, 0u);
-    }
-    SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
-               (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
-    sweep(X, 0u);
-}
-
-}  // namespace aspgpu
-
-// ------------------------------------------------------------ launchers
-
-namespace aspgpu {
-
-// The dynamic shared-memory limit is a property of the kernel, shared by
+// The dynamic shared-memory limit is a property of each kernel, shared by
 // every program: it is set to the largest size any program may use, and
-// occupancy is computed for this program's own size.
+// occupancy is computed for a program's own size.
 constexpr int MAX_DYN_SMEM = 220 * 1024;
-
-cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm)
-{
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block, smem);
-}
-
-cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st)
-{
-    Dev copy = D;
-    void *args[] = {(void *)&copy};
-    return cudaLaunchCooperativeKernel((void *)solve_kernel, dim3(grid), dim3(block), args, smem, st);
-}
-
-cudaError_t batch_configure(size_t smem, int *blocks_per_sm)
-{
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem);
-}
-
-cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
-                         size_t smem, cudaStream_t st)
-{
-    batch_kernel<<<grid, 256, smem, st>>>(devs, order, n, queue);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st,
-                         uint32_t passes)
-{
-    sweep_kernel<<<grid, block, smem, st>>>(D, acc, passes);
-    return cudaGetLastError();
-}
 
 }  // namespace aspgpu
