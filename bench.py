@@ -221,8 +221,9 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.synchronize(dev)
 
     totals = dict(literal_checks=0, propagations=0, decisions=0, conflicts=0, rounds=0,
+                  max_level=0, learned=0, learned_literals=0,
                   ns_total=0, ns_sweep=0, ns_analysis=0, ns_decision=0, ns_stability=0,
-                  ns_buckets=0, ns_learned=0, ns_barrier=0)
+                  ns_buckets=0, ns_learned=0, ns_barrier=0, ns_slowest_cta=0, ns_slowest_sweep=0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     statuses = []
     barrier()
@@ -235,7 +236,7 @@ def run_ours(a, rank, world, local_rank):
             torch.cuda.synchronize(dev)
             s = P.stats()
             for k in totals:
-                totals[k] += s[k]
+                totals[k] = max(totals[k], s[k]) if k == "max_level" else totals[k] + s[k]
             statuses.append(int(d_result[0].item()))
         barrier()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
@@ -329,9 +330,12 @@ def run_ours(a, rank, world, local_rank):
             "search": {"statuses": statuses, "decisions_per_s": totals["decisions"] / tsec,
                        "propagations_per_s": totals["propagations"] / tsec,
                        "conflicts_per_s": totals["conflicts"] / tsec, "rounds_per_s": totals["rounds"] / tsec,
+                       "max_level": int(totals["max_level"]),
+                       "learned_avg_len": totals["learned_literals"] / max(totals["learned"], 1),
                        "device_ns": {k: totals[k] for k in ("ns_total", "ns_sweep", "ns_analysis",
                                                            "ns_decision", "ns_stability", "ns_buckets",
-                                                           "ns_learned", "ns_barrier")}},
+                                                           "ns_learned", "ns_barrier", "ns_slowest_cta",
+                                                           "ns_slowest_sweep")}},
             "solver_src_sha": sha,
         }
     if world > 1:

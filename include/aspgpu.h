@@ -114,6 +114,8 @@ typedef struct {
                                                    nogoods, waiting at phase barriers */
     int64_t view_mode, batch_view_mode;         /* ASP_VIEW_* chosen for asp_solve and for
                                                    asp_solve_batch */
+    int64_t ns_slowest_cta, ns_slowest_sweep;   /* sums over phases of the slowest CTA's time
+                                                   before the phase barrier, and in the sweep */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */

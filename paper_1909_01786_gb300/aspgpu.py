@@ -49,7 +49,7 @@ class Stats(C.Structure):
         "propagations", "conflicts", "decisions", "completions", "learned",
         "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
         "ns_sweep", "ns_analysis", "ns_decision", "ns_stability", "ns_buckets", "ns_learned",
-        "ns_barrier", "view_mode", "batch_view_mode")]
+        "ns_barrier", "view_mode", "batch_view_mode", "ns_slowest_cta", "ns_slowest_sweep")]
 
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",

@@ -459,7 +459,7 @@ static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t m
     ctl[0].lfill = D.lits_static;
     for (int i = 0; i < 4; i++) {
         acc[i].ckey = NO_KEY; acc[i].dkey = 0; acc[i].nclaim = 0; acc[i].flag = 0;
-        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0;
+        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0; acc[i].tbusy = 0; acc[i].tsweep = 0;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.acc, acc, sizeof(acc), cudaMemcpyHostToDevice, st);
@@ -489,6 +489,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.ns_decision = (int64_t)s.ns_decision; o.ns_stability = (int64_t)s.ns_stab;
     o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
     o.view_mode = D.view_mode; o.batch_view_mode = p->D1.view_mode;
+    o.ns_slowest_cta = (int64_t)s.ns_slowest; o.ns_slowest_sweep = (int64_t)s.ns_slowest_sweep;
 }
 
 extern "C" {
@@ -584,7 +585,7 @@ int asp_debug_propagate(asp_prog *p, const int8_t *partial, int8_t *closure, int
         if (partial[v] == 0) continue;
         uint32_t code = partial[v] > 0 ? V_T : V_F;
         asg[v >> 3] |= code << ((v & 7u) * 4u);
-        trail.push_back(v);
+        trail.push_back(v | (code == V_F ? TRAIL_F : 0u));
         dl[v] = 1;
     }
     cudaStream_t st = p->stream;
@@ -621,6 +622,7 @@ int asp_sweep(asp_prog *p, int32_t passes)
     if (!p || passes < 1) return fail(ASP_E_ARG, "bad argument");
     Acc a;
     a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+    a.tbusy = 0; a.tsweep = 0;
     cudaError_t e = cudaMemcpyAsync(p->d_sweep_acc, &a, sizeof(a), cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep reset");
     e = launch_sweep(p->D, p->d_sweep_acc, p->grid, p->block, p->smem, p->stream, (uint32_t)passes);
@@ -640,7 +642,10 @@ int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *leve
     if (e != cudaSuccess) return cuda_fail(e, "state");
     int64_t nt = std::min<int64_t>((int64_t)s.pad, (int64_t)D.nv);
     if (n_trail) *n_trail = nt;
-    if (trail && nt > 0) e = cudaMemcpy(trail, D.trail, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+    if (trail && nt > 0) {
+        e = cudaMemcpy(trail, D.trail, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < nt; i++) trail[i] = (int32_t)((uint32_t)trail[i] & TRAIL_VAR);
+    }
     if (e == cudaSuccess && level) e = cudaMemcpy(level, D.dl, (size_t)D.nv * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && reason) e = cudaMemcpy(reason, D.reason, (size_t)D.nv * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && deps && deps_words > 0) {

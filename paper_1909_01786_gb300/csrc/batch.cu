@@ -6,7 +6,7 @@ namespace aspgpu {
 
 // Batched solving: each CTA takes programs from a queue (the host orders it
 // largest first) and solves each alone, with the whole program's assignment
-// view in its shared memory and __syncthreads as the phase barrier.
+// view in its shared memory and a CTA barrier as the phase barrier.
 __global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
                                                        unsigned int *queue)
 {
@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const ui
             s_item = i < n ? __ldg(order + i) : 0xFFFFFFFFu;
             if (s_item != 0xFFFFFFFFu) sD = devs[s_item];
         }
-        __syncthreads();
+        cta_sync();
         if (s_item == 0xFFFFFFFFu) break;
         const Dev &D = sD;
         // reset this program's search state
@@ -36,16 +36,16 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const ui
             memset(&c, 0, sizeof(c));
             D.ctl[1] = c;
             Acc a;
-            a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+            a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.tbusy = 0; a.tsweep = 0;
             for (int i = 0; i < 4; i++) D.acc[i] = a;
             memset(D.stats, 0, sizeof(DevStats));
             memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check
         }
-        __syncthreads();
+        cta_sync();
         const Smem S = make_smem(D, smem_raw);
         const View V = make_view(D, S.misc + 16, 0);
         solver_loop<true>(D, S, V, threadIdx.x, blockDim.x, true, threadIdx.x == 0, 0);
-        __syncthreads();
+        cta_sync();
     }
 }
 

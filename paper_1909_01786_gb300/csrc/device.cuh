@@ -20,6 +20,12 @@ constexpr uint32_t R_INPUT = 0xFFFFFFFDu;
 //   only ever computed from committed variables.
 constexpr uint32_t V_T = 1u, V_F = 2u;
 
+// Trail entries: the variable, with TRAIL_F set if it was made false (so a
+// round can put the previous round's claims into its views without reading
+// the codes).
+constexpr uint32_t TRAIL_F = 0x80000000u;
+constexpr uint32_t TRAIL_VAR = 0x7FFFFFFFu;
+
 enum Op : uint32_t {
     OP_INIT = 1,      // InitialPropagation: apply the unit nogoods at level 1
     OP_ROUND,         // commit last round's claims, then propagate-and-check sweep
@@ -68,6 +74,8 @@ struct Acc {              // per-phase accumulators, indexed by phase % 4
     uint32_t minU;              // smallest unfounded true atom
     uint32_t nlits;             // literals appended to the loop nogood
     unsigned long long checks;  // literals classified by long/learned sweeps
+    unsigned long long tbusy;   // max over CTAs of the time from phase start to barrier arrival
+    unsigned long long tsweep;  // max over CTAs of the time in the sweep
 };
 
 struct DevStats {
@@ -78,10 +86,15 @@ struct DevStats {
     // time inside sweeps seen by CTA 0: static buckets, long and learned
     // nogoods, and waiting at the phase barrier
     unsigned long long ns_buckets, ns_learned, ns_barrier, pad2;
+    // sums over phases of the slowest CTA's busy time and sweep time
+    unsigned long long ns_slowest, ns_slowest_sweep;
     unsigned int trace_n, pad4;    // trace records written (atomic)
 };
 
-struct Barrier { unsigned int count, gen, err, pad; };
+// Grid barrier: arrivals counted since the solve began (barrier g is
+// complete once count >= (g + 1) * CTAs); err is set by a CTA that gave up
+// waiting.
+struct Barrier { unsigned long long count; unsigned int err, pad; };
 
 struct Dev {
     uint32_t na, J, nv, asg_words;

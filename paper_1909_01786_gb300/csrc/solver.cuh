@@ -34,6 +34,16 @@ namespace aspgpu {
 
 #define FULL_MASK 0xFFFFFFFFu
 
+// CTA barrier that counts every thread on its own (PTX barrier.sync
+// without .aligned).  The aligned form counts a warp as arrived when its
+// first threads get there, which let warps pass while lane 0 of another
+// warp was still finishing a section it runs alone (an atomic reservation,
+// a control-block copy) and read shared values before they were written.
+__device__ __forceinline__ void cta_sync()
+{
+    asm volatile("barrier.sync 0;" ::: "memory");
+}
+
 // ------------------------------------------------------------ primitives
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
@@ -50,40 +60,47 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Grid barrier with a bounded wait: returns false (and sets the sticky error
-// flag) if the other CTAs do not arrive within ~20 s.
+// flag) if the other CTAs do not arrive within ~20 s, or if another CTA gave
+// up.  One atomic per CTA on a counter that is never reset: the barrier an
+// arrival belongs to is its count divided by the number of CTAs.
 __device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks)
 {
     __shared__ int s_ok;
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 0) {
         int ok = 1;
         if (nblocks > 1) {
-            unsigned g = ld_acquire_u32(&b->gen);
             __threadfence();
-            unsigned arrived = atomicAdd(&b->count, 1u);
-            if (arrived == nblocks - 1) {
-                atomicExch(&b->count, 0u);
-                __threadfence();
-                atomicAdd(&b->gen, 1u);
-            } else {
-                unsigned long long t0 = globaltimer_ns();
-                unsigned spins = 0;
-                while (ld_acquire_u32(&b->gen) == g) {
-                    if (ld_acquire_u32(&b->err)) { ok = 0; break; }
-                    if ((++spins & 1023u) == 0 && globaltimer_ns() - t0 > 20000000000ull) {
-                        atomicExch(&b->err, 1u);
-                        ok = 0;
-                        break;
+            const unsigned long long old = atomicAdd(&b->count, 1ull);
+            const unsigned long long target = (old / nblocks + 1ull) * nblocks;
+            if (old + 1ull != target) {
+                unsigned long long t0 = 0;
+                for (unsigned spins = 1; ld_acquire_u64(&b->count) < target; spins++) {
+                    if ((spins & 255u) == 0u) {
+                        if (ld_acquire_u32(&b->err)) { ok = 0; break; }
+                        const unsigned long long now = globaltimer_ns();
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > 20000000000ull) {
+                            atomicExch(&b->err, 1u);
+                            ok = 0;
+                            break;
+                        }
                     }
                 }
             }
+            __threadfence();
         }
-        __threadfence();
-        if (ld_acquire_u32(&b->err)) ok = 0;
         s_ok = ok;
     }
-    __syncthreads();
+    cta_sync();
     return s_ok != 0;
 }
 
@@ -306,7 +323,17 @@ struct SweepCtx {
                            // and bitmap are known here before they reach memory)
     uint32_t cta;          // this CTA's part of the static partition
     uint32_t gw, nw;       // warp index and warp count of the solving group
+    // inside a sweep: claims are listed in shared memory and copied to the
+    // trail once at the end of the sweep (one global atomic per CTA)
+    bool listed = false;
 };
+
+constexpr uint32_t CLAIM_BUF = 256;
+__shared__ uint32_t s_claims[CLAIM_BUF];
+__shared__ unsigned int s_ncl, s_cbase;
+// CTA 0, thread 0: time in the sweeps on long and learned nogoods and on
+// the buckets
+__shared__ unsigned long long s_tlearned, s_tbuckets;
 
 __device__ __forceinline__ void report_conflict(const SweepCtx &X, uint32_t id, uint32_t len)
 {
@@ -314,13 +341,18 @@ __device__ __forceinline__ void report_conflict(const SweepCtx &X, uint32_t id, 
 }
 
 // Record a won claim: trail slot, level, reason.
-__device__ __forceinline__ void record_claim(const SweepCtx &X, uint32_t v, uint32_t id)
+__device__ __forceinline__ void record_claim(const SweepCtx &X, uint32_t v, uint32_t valbit, uint32_t id)
 {
     const Dev &D = *X.D;
-    uint32_t pos = X.tbase + atomicAdd(&X.acc->nclaim, 1u);
-    if (pos < D.nv) D.trail[pos] = v;
     D.dl[v] = (int32_t)X.cdl;
     D.reason[v] = id;
+    const uint32_t entry = v | (valbit == V_F ? TRAIL_F : 0u);
+    if (X.listed) {
+        const uint32_t i = atomicAdd(&s_ncl, 1u);
+        if (i < CLAIM_BUF) { s_claims[i] = entry; return; }
+    }
+    uint32_t pos = X.tbase + atomicAdd(&X.acc->nclaim, 1u);
+    if (pos < D.nv) D.trail[pos] = entry;
 }
 
 // One lane per literal u of a reason (has = false on lanes holding none):
@@ -384,6 +416,36 @@ __device__ __forceinline__ void lane_deps(const SweepCtx &X, const uint32_t (&va
     }
 }
 
+// Dependency bitmap of x (claimed by one lane) computed by the whole warp:
+// every lane loads the levels of the nogood's other variables (the same
+// addresses, one transaction each) and ORs the bitmap words w = lane,
+// lane + 32, ... over those with level > 1 (Section 4.2, mk_dl_bitmap), so a
+// claim costs two dependent loads whatever the bitmap width.  All 32 lanes
+// call it with the same arguments.
+template <int L>
+__device__ __forceinline__ void warp_deps(const SweepCtx &X, const uint32_t (&var)[L], uint32_t x)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nw = deps_words(D, X.cdl);
+    const uint32_t dbit = level_bit(D, X.cdl);
+    int32_t Lu[L];
+    bool has_dec = false;
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+        const uint32_t u = var[q];
+        has_dec |= u != x && u == X.dec_v;
+        Lu[q] = (u != x && u != X.dec_v) ? __ldcg(D.dl + u) : 0;
+    }
+    for (uint32_t w = lane; w < nw; w += 32u) {
+        unsigned long long acc = (has_dec && w == (dbit >> 6)) ? (1ull << (dbit & 63u)) : 0ull;
+#pragma unroll
+        for (int q = 0; q < L; q++)
+            if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= __ldcg(D.deps + (size_t)var[q] * D.WW + w);
+        D.deps[(size_t)x * D.WW + w] = acc;
+    }
+}
+
 // U groups of 32 nogoods of bucket L, lane = nogood k0 + t*stride + lane.
 // All literals are loaded (coalesced, one row per literal position) and
 // their values gathered before any is classified: a nogood is satisfied if
@@ -431,7 +493,7 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
             const int r = claim_var(D.asg, x, valbit, X.fresh);
             if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
             if (r != 0) continue;
-            record_claim(X, x, id);
+            record_claim(X, x, valbit, id);
             if (X.cdl > 1u) {
                 uint32_t var[L];
 #pragma unroll
@@ -495,35 +557,63 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
 #pragma unroll
         for (int t = 0; t < U; t++) {
             const uint32_t k = k0 + (uint32_t)t * 32u + lane;
-            if (k >= k1 || (cnt[t] & 0xFFu) > 1u) continue;
-            const uint32_t id = bucket_nogood_id((uint32_t)L, k);
-            // violated or unit: classify again from the current view (a
-            // claim of this CTA may have changed it since the count)
-            bool sat = false;
-            uint32_t n_un = 0, ul = 0;
+            bool won = false;
+            uint32_t e = 0, x = 0, valbit = 0;
+            if (k < k1 && (cnt[t] & 0xFFu) <= 1u) {
+                const uint32_t id = bucket_nogood_id((uint32_t)L, k);
+                // violated or unit: classify again from the current view (a
+                // claim of this CTA may have changed it since the count)
+                bool sat = false;
+                uint32_t n_un = 0, ul = 0;
 #pragma unroll
-            for (int q = 0; q < L; q++) {
-                const uint32_t tv = (tlit_val<BYTES>(X.V, lit[t][q]) ^ lit[t][q]) & 3u;
-                sat |= tv == 2u;
-                if (tv == 0u || tv == 3u) { n_un++; ul = lit[t][q]; }
+                for (int q = 0; q < L; q++) {
+                    const uint32_t tv = (tlit_val<BYTES>(X.V, lit[t][q]) ^ lit[t][q]) & 3u;
+                    sat |= tv == 2u;
+                    if (tv == 0u || tv == 3u) { n_un++; ul = lit[t][q]; }
+                }
+                if (!sat && n_un == 0u) {
+                    report_conflict(X, id, (uint32_t)L);
+                } else if (!sat && n_un == 1u) {
+                    if (!X.do_claim) {
+                        atomicAdd(&X.acc->flag, 1u);
+                    } else {
+                        e = ul >> 2;
+                        x = X.V.var(e);
+                        valbit = (ul & 1u) ? V_T : V_F;
+                        const int r = claim_var(D.asg, x, valbit, X.fresh);
+                        if (r == 2) report_conflict(X, id, (uint32_t)L);
+                        else if (r == 0) { record_claim(X, x, valbit, id); won = true; }
+                    }
+                }
             }
-            if (sat || n_un > 1u) continue;
-            if (n_un == 0u) { report_conflict(X, id, (uint32_t)L); continue; }
-            if (!X.do_claim) { atomicAdd(&X.acc->flag, 1u); continue; }
-            const uint32_t e = ul >> 2, x = X.V.var(e), valbit = (ul & 1u) ? V_T : V_F;
-            const int r = claim_var(D.asg, x, valbit, X.fresh);
-            if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
-            if (r != 0) continue;
-            record_claim(X, x, id);
-            if (X.cdl > 1u) {
+            if (L > 8 && won && X.cdl > 1u) {
+                // long buckets (few claims): the claiming lane alone
                 uint32_t var[L];
 #pragma unroll
                 for (int q = 0; q < L; q++) var[q] = X.V.var(lit[t][q] >> 2);
                 lane_deps<L>(X, var, x);
             }
-            __threadfence_block();
-            X.V.put(e, valbit);
-            pub = true;
+            if (L <= 8 && X.cdl > 1u) {
+                // bitmaps of this group's claims, one claim at a time, by the warp
+                unsigned m = __ballot_sync(FULL_MASK, won);
+                if (m) {
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1u;
+                        uint32_t var[L];
+#pragma unroll
+                        for (int q = 0; q < L; q++) var[q] = X.V.var(__shfl_sync(FULL_MASK, lit[t][q], src) >> 2);
+                        warp_deps<L>(X, var, __shfl_sync(FULL_MASK, x, src));
+                    }
+                    __threadfence_block();
+                    __syncwarp();
+                }
+            }
+            if (won) {
+                __threadfence_block();
+                X.V.put(e, valbit);
+                pub = true;
+            }
         }
         if (!X.do_claim || !__any_sync(FULL_MASK, pub)) break;
     }
@@ -625,7 +715,7 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
             } else {
                 uint32_t v = ulit >> 1, valbit = (ulit & 1u) ? V_T : V_F;
                 int r = claim_var(D.asg, v, valbit, X.fresh);
-                if (r == 0) { record_claim(X, v, id); won = 1; }
+                if (r == 0) { record_claim(X, v, valbit, id); won = 1; }
                 else if (r == 2) report_conflict(X, id, len);
             }
         }
@@ -655,8 +745,10 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
 
 // Propagate-and-check over this CTA's ranges of every bucket, then
 // (grid-wide) the static long nogoods and the learned nogoods.
-__device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
+__device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned)
 {
+    SweepCtx X = X0;
+    X.listed = X0.do_claim;
     const Dev &D = *X.D;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t G1 = D.G + 1u;
@@ -667,9 +759,9 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
     // every warp runs about the same number of load-gather-classify chains
     // whatever the mix of lengths.
     __shared__ unsigned int s_unit;
-    __syncthreads();                       // the previous sweep's warps are done with it
-    if (threadIdx.x == 0) s_unit = 0u;
-    __syncthreads();
+    cta_sync();                       // the previous sweep's warps are done with it
+    if (threadIdx.x == 0) { s_unit = 0u; s_ncl = 0u; }
+    cta_sync();
     uint32_t ubase[BUCKET_MAX + 2];
     ubase[2] = 0u;
 #pragma unroll
@@ -679,6 +771,17 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
         ubase[L + 1] = ubase[L] + (groups + per - 1u) / per;
     }
     const uint32_t units = ubase[BUCKET_MAX + 1];
+    // Long and learned nogoods first (one warp each, round-robin over CTAs
+    // first, then over the warps of a CTA); the warps that take one then
+    // take fewer bucket units from the queue.
+    unsigned long long checks = 0;
+    const uint32_t nl = D.n_long + n_learned;
+    const uint32_t wpc = blockDim.x >> 5, slot = (X.gw % wpc) * (X.nw / wpc) + X.gw / wpc;
+    for (uint32_t i = slot; i < nl; i += X.nw) {
+        uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
+        classify_long(X, id, checks);
+    }
+    const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
     for (;;) {
         uint32_t u = 0;
         if (lane == 0) u = atomicAdd(&s_unit, 1u);
@@ -695,18 +798,27 @@ __device__ __forceinline__ void sweep(const SweepCtx &X, uint32_t n_learned)
         else if (D.view_mode == VIEW_PACKED) run_unit_view<false>(X, L, k0, b1);
         else run_unit(X, L, k0, b1);
     }
-    unsigned long long checks = 0;
-    const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
-    const uint32_t nl = D.n_long + n_learned;
-    for (uint32_t i = X.gw; i < nl; i += X.nw) {
-        uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
-        classify_long(X, id, checks);
-    }
     if (lane == 0 && checks) atomicAdd(&X.acc->checks, checks);
     if (timer) {
         const unsigned long long t2 = globaltimer_ns();
-        D.stats->ns_buckets += t1 - t0;
-        D.stats->ns_learned += t2 - t1;
+        s_tlearned += t1 - t0;
+        s_tbuckets += t2 - t1;
+    }
+    if (X.do_claim) {
+        // copy the listed claims to the trail: warp 0 reserves the slots,
+        // then every thread copies (no barrier under a data-dependent branch)
+        cta_sync();
+        const uint32_t n = min(s_ncl, CLAIM_BUF);
+        if (threadIdx.x < 32u) {
+            uint32_t base = 0;
+            if (threadIdx.x == 0 && n) base = atomicAdd(&X.acc->nclaim, n);
+            base = __shfl_sync(FULL_MASK, base, 0);
+            if (threadIdx.x == 0) s_cbase = X.tbase + base;
+        }
+        cta_sync();
+        const uint32_t b = s_cbase;
+        for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
+            if (b + k < D.nv) D.trail[b + k] = s_claims[k];
     }
 }
 
@@ -850,7 +962,7 @@ __device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, ui
     best = shfl_max_u64(best);
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     if (lane == 0) S.red[wid] = best;
-    __syncthreads();
+    cta_sync();
     if (wid == 0) {
         unsigned long long x = lane < (blockDim.x >> 5) ? S.red[lane] : 0ull;
         x = shfl_max_u64(x);
@@ -879,7 +991,7 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
         S.misc[4] = len;
         S.misc[5] = clash;
     }
-    __syncthreads();
+    cta_sync();
     const uint32_t len = S.misc[4], clash = S.misc[5];
     for (uint32_t t = tid; t < len * nw; t += nt) {
         uint32_t i = t / nw, w = t % nw;
@@ -900,7 +1012,7 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
                 if (L > 1 && w < deps_words(D, (uint32_t)L)) atomicOr(&S.bm[w], __ldcg(D.deps + (size_t)clash * D.WW + w));
         }
     }
-    __syncthreads();
+    cta_sync();
     if (tid == 0) {
         bool overflow = cdl >= D.Wlevels && (S.bm[D.WW - 1] >> 63);
         int top = -1;
@@ -947,7 +1059,7 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
             }
         }
     }
-    __syncthreads();
+    cta_sync();
 }
 
 __device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase, uint32_t cta)
@@ -989,7 +1101,7 @@ template <bool BATCH>
 __device__ __forceinline__ bool group_sync(const Dev &D)
 {
     if (BATCH) {
-        __syncthreads();
+        cta_sync();
         return true;
     }
     return grid_sync(D.bar, gridDim.x);
@@ -1006,26 +1118,35 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     __shared__ Ctl sC;
     __shared__ Acc sA;
     const uint32_t gtid = rank, nthreads = size;
-    unsigned long long t_start = 0, t_phase = 0;
-    if (leader) { t_start = globaltimer_ns(); t_phase = t_start; }
+    // leader-only counters (shared memory, not registers of every thread),
+    // written to the stats when the search ends
+    __shared__ unsigned long long t_start, t_phase, n_conf, n_phases, ns_bar, ns_sw, ns_an, ns_de, ns_st;
+    __shared__ unsigned long long ns_slow, ns_slow_sw, t_cta0;
+    if (leader) {
+        t_start = globaltimer_ns();
+        t_phase = t_start;
+        n_conf = n_phases = ns_bar = ns_sw = ns_an = ns_de = ns_st = ns_slow = ns_slow_sw = 0ull;
+    }
+    if (threadIdx.x == 0) { s_tlearned = 0ull; s_tbuckets = 0ull; t_cta0 = globaltimer_ns(); }
 
     if (threadIdx.x == 0) ldcg_copy(&sC, D.ctl);
     if (D.heuristic == 2) {
         uint16_t *w = const_cast<uint16_t *>(reinterpret_cast<const uint16_t *>(S.mlp));
         for (uint32_t i = threadIdx.x; i < (uint32_t)MLP_PARAMS; i += blockDim.x) w[i] = __ldg(D.mlp + i);
     }
-    __syncthreads();
+    cta_sync();
     view_reload(D, V, 4u << (sC.round & 1u));
-    __syncthreads();
+    cta_sync();
 
     for (uint32_t k = 0;; k++) {
         if (threadIdx.x == 0) {
             ldcg_copy(&sC, D.ctl + (k & 1u));
             ldcg_copy(&sA, D.acc + ((k + 3u) & 3u));
         }
-        __syncthreads();
+        cta_sync();
         const Ctl C = sC;
         const Acc A = sA;
+        if (leader) { ns_slow += A.tbusy; ns_slow_sw += A.tsweep; }
         if (C.op == OP_DONE) break;
         Acc *acc = D.acc + (k & 3u);
         // the next control block, written by the leader only (kept in
@@ -1052,8 +1173,9 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 uint32_t val = global_val(D, v, fresh_cur);
                 uint32_t own = (l & 1u) ? V_F : V_T;
                 if (val == 0u) {
-                    int r = claim_var(D.asg, v, (l & 1u) ? V_T : V_F, fresh_cur);
-                    if (r == 0) record_claim(X, v, id);
+                    const uint32_t valbit = (l & 1u) ? V_T : V_F;
+                    int r = claim_var(D.asg, v, valbit, fresh_cur);
+                    if (r == 0) record_claim(X, v, valbit, id);
                     else if (r == 2) report_conflict(X, id, 1u);
                 } else if (val == own) {
                     report_conflict(X, id, 1u);
@@ -1073,6 +1195,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                         N.conflict = 1;
                         N.status = C.n_models > 0 ? 10 : 20;
                         atomicAdd(&D.stats->conflicts, 1ull);
+                        n_conf++;
                     }
                     break;
                 }
@@ -1081,6 +1204,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     analyze(D, S, g, C.cdl, C.lfill, true);
                     if (leader) {
                         atomicAdd(&D.stats->conflicts, 1ull);
+                        n_conf++;
                         if (S.misc[0]) {
                             N.op = OP_DONE;
                             N.status = C.n_models > 0 ? 10 : 20;
@@ -1122,19 +1246,19 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             // make last round's claims visible: clear their fresh bit
             // (grid-wide) and put them in this CTA's view
             for (uint32_t i = C.tc + gtid; i < tend; i += nthreads) {
-                uint32_t v = __ldcg(D.trail + i);
+                uint32_t v = __ldcg(D.trail + i) & TRAIL_VAR;
+                if (v >= D.nv) { atomicExch(&D.bar->err, 2u); continue; }   // corrupt trail: stop with an error
                 atomicAnd(D.asg + (v >> 3), ~(fresh_prev << ((v & 7u) * 4u)));
             }
             if (tend - C.tc > 4096u) {
                 view_reload(D, V, fresh_cur);
             } else {
                 for (uint32_t i = C.tc + threadIdx.x; i < tend; i += blockDim.x) {
-                    uint32_t v = __ldcg(D.trail + i);
-                    uint32_t val = nib(__ldcg(D.asg + (v >> 3)), v) & 3u;
-                    if (val == V_T || val == V_F) view_set(V, v, val);
+                    const uint32_t e = __ldcg(D.trail + i);
+                    view_set(V, e & TRAIL_VAR, (e & TRAIL_F) ? V_F : V_T);
                 }
             }
-            __syncthreads();
+            cta_sync();
             sw = true; sw_cdl = C.cdl; sw_tbase = tend;
             if (leader) {
                 N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1;
@@ -1154,7 +1278,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 for (uint32_t p = gtid; p < D.na; p += nthreads) {
                     if ((nib(__ldcg(D.asg + (p >> 3)), p) & 3u) != 0u) continue;
                     if (claim_var(D.asg, p, V_F, fresh_cur) == 0) {
-                        record_claim(X, p, R_COMPLETE);
+                        record_claim(X, p, V_F, R_COMPLETE);
                         if (C.cdl > 1u)
                             for (uint32_t w = 0; w < nw; w++)
                                 D.deps[(size_t)p * D.WW + w] = all_levels_word(D, C.cdl, w);
@@ -1182,7 +1306,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 atomicOr(D.asg + (bv >> 3), V_T << ((bv & 7u) * 4u));
             }
             if (threadIdx.x == 0) view_set(V, bv, V_T);
-            __syncthreads();
+            cta_sync();
             sw = true; sw_cdl = L; sw_tbase = tend + 1u; sw_dec = bv;
             if (leader) {
                 N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
@@ -1198,12 +1322,13 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             kind = 1;
             const uint32_t newend = __ldcg(D.level_start + C.target + 1u);
             for (uint32_t i = newend + gtid; i < tend; i += nthreads) {
-                uint32_t v = __ldcg(D.trail + i);
+                uint32_t v = __ldcg(D.trail + i) & TRAIL_VAR;
+                if (v >= D.nv) { atomicExch(&D.bar->err, 2u); continue; }
                 atomicAnd(D.asg + (v >> 3), ~(0xFu << ((v & 7u) * 4u)));
                 D.dl[v] = 0;
             }
             for (uint32_t i = newend + threadIdx.x; i < tend; i += blockDim.x)
-                view_clear(V, __ldcg(D.trail + i));
+                view_clear(V, __ldcg(D.trail + i) & TRAIL_VAR);
             if (leader) {
                 N.op = OP_ROUND; N.cdl = C.target; N.tc = newend; N.tb = newend; N.clean = 0;
             }
@@ -1338,11 +1463,12 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     D.learned_ids[C.n_learned] = C.lfill;
                     __threadfence();
                 }
-                __syncthreads();
+                cta_sync();
                 const uint32_t lf = C.lfill + len;
                 analyze(D, S, C.conf_id, C.cdl, lf, false);
                 if (leader) {
                     atomicAdd(&D.stats->conflicts, 1ull);
+                    n_conf++;
                     atomicAdd(&D.stats->learned, 1ull);
                     atomicAdd(&D.stats->learned_lits, (unsigned long long)len);
                     if (S.misc[0]) {
@@ -1369,40 +1495,56 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             break;
         }
         if (sw) {
+            const unsigned long long ts = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
             SweepCtx X{&D, V, fresh_cur, sw_cdl, sw_tbase, acc, true, true, sw_dec, cta, rank >> 5, size >> 5};
             sweep(X, C.n_learned);
+            if (threadIdx.x == 0) atomicMax(&acc->tsweep, globaltimer_ns() - ts);
         }
 
         if (leader) {
             if (D.mode == MODE_SOLVE && N.op != OP_DONE) {
                 unsigned long long now = globaltimer_ns();
                 bool over_time = D.time_budget_ns > 0 && (long long)(now - t_start) > D.time_budget_ns;
-                bool over_conf = D.conflict_budget > 0 && (long long)__ldcg(&D.stats->conflicts) >= D.conflict_budget;
+                bool over_conf = D.conflict_budget > 0 && (long long)n_conf >= D.conflict_budget;
                 if (over_time || over_conf) { N.op = OP_DONE; N.status = N.n_models > 0 ? 10 : 0; }
             }
             D.ctl[(k + 1u) & 1u] = N;
             Acc z;
             z.ckey = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0;
+            z.tbusy = 0; z.tsweep = 0;
             D.acc[(k + 1u) & 3u] = z;
             // fold long-nogood checks of the previous phase into the stats
             if (A.checks) atomicAdd(&D.stats->checks, A.checks);
             unsigned long long now = globaltimer_ns();
             unsigned long long dt = now - t_phase;
             t_phase = now;
-            unsigned long long *bucket = kind == 0 ? &D.stats->ns_sweep : kind == 1 ? &D.stats->ns_analysis
-                                       : kind == 2 ? &D.stats->ns_decision : &D.stats->ns_stab;
-            *bucket += dt;
-            D.stats->phases += 1;
+            if (kind == 0) ns_sw += dt;
+            else if (kind == 1) ns_an += dt;
+            else if (kind == 2) ns_de += dt;
+            else ns_st += dt;
+            n_phases++;
             __threadfence();
         }
-        const unsigned long long tb0 = (cta0 && threadIdx.x == 0) ? globaltimer_ns() : 0ull;
+        const unsigned long long tb0 = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
+        if (threadIdx.x == 0) atomicMax(&acc->tbusy, tb0 - t_cta0);
         if (!group_sync<BATCH>(D)) break;
-        if (cta0 && threadIdx.x == 0) D.stats->ns_barrier += globaltimer_ns() - tb0;
+        if (threadIdx.x == 0) t_cta0 = globaltimer_ns();
+        if (leader) ns_bar += t_cta0 - tb0;
     }
     if (leader) {
         const Ctl F = sC;
         D.stats->pad = F.tc;
         D.stats->ns_total = globaltimer_ns() - t_start;
+        D.stats->ns_sweep = ns_sw;
+        D.stats->ns_analysis = ns_an;
+        D.stats->ns_decision = ns_de;
+        D.stats->ns_stab = ns_st;
+        D.stats->phases = n_phases;
+        D.stats->ns_barrier = ns_bar;
+        D.stats->ns_learned = s_tlearned;
+        D.stats->ns_buckets = s_tbuckets;
+        D.stats->ns_slowest = ns_slow;
+        D.stats->ns_slowest_sweep = ns_slow_sw;
         int err = F.err;
         if (__ldcg(&D.bar->err)) err = -6;
         D.result[0] = F.status;
