@@ -147,13 +147,48 @@ int asp_solve_async(asp_prog *p, int64_t max_models, uint64_t *d_models, int64_t
                     int64_t *d_result);
 
 /* Solve n independent programs in one persistent launch, one CTA per program
- * at a time, taking programs from a device work queue largest first.
- * progs[i] must have been loaded with the same stream.  statuses[i],
- * n_models[i] are host outputs; models[i] (host, models_cap[i] rows) may be
- * NULL when models_cap[i] is 0. */
+ * at a time, taking programs from a device work queue largest first (not in
+ * the paper, which solves one program per run).  progs[i] must have been
+ * loaded with the same stream.  statuses[i], n_models[i] are host outputs;
+ * models[i] (host, models_cap[i] rows) may be NULL when models_cap[i] is 0.
+ * Same as asp_batch_create (configuration 0) + asp_batch_run +
+ * asp_batch_free. */
 int asp_solve_batch(int32_t n, asp_prog *const *progs, int64_t max_models_each,
                     int32_t *statuses, int64_t *n_models, uint64_t *const *models,
                     const int64_t *models_cap);
+
+/* A batch prepared for repeated solving (not in the paper). */
+typedef struct asp_batch asp_batch;
+
+#define ASP_BATCH_AUTOTUNE (-1)   /* let the autotuner choose the configuration */
+
+/* Prepare repeated batched solving of n loaded programs: uploads one
+ * descriptor per program, chooses the kernel configuration and captures the
+ * launch (queue reset + batch kernel) in a CUDA graph.  Configurations:
+ * 0 = 256 threads per CTA, 3 CTAs per SM; 1 = 128 threads, 6 per SM (twice
+ * the programs in flight, smaller shared-memory views).  config =
+ * ASP_BATCH_AUTOTUNE runs each configuration once on a sample of up to 512
+ * programs spread over the queue and keeps the one with the lower device
+ * time per program (the trial solves change nothing but the programs' last
+ * results).  models_cap may be NULL (no models kept).  The programs must
+ * stay loaded until asp_batch_free.  Errors: ASP_E_ARG, ASP_E_OOM,
+ * ASP_E_CUDA. */
+int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each, const int64_t *models_cap,
+                     int32_t config, asp_batch **out);
+
+/* Replay the captured launch: every program of the batch is solved from
+ * scratch.  Outputs and errors as asp_solve_batch (models[i] may be NULL
+ * when the capacity given at creation is 0). */
+int asp_batch_run(asp_batch *b, int32_t *statuses, int64_t *n_models, uint64_t *const *models);
+
+/* The configuration in use (0 or 1), its threads per CTA, the grid, and the
+ * autotuner's device time per program of configurations 0 and 1 (ns; 0 if
+ * not measured, < 0 if it could not run); any output may be NULL. */
+int asp_batch_info(const asp_batch *b, int32_t *config, int32_t *block_threads, int32_t *grid,
+                   double *trial_ns);
+
+/* Release the batch's descriptors, graph and stream (not the programs). */
+void asp_batch_free(asp_batch *b);
 
 /* Counters of the last solve on this program (device time in ns). */
 int asp_stats(const asp_prog *p, asp_stats_t *out);

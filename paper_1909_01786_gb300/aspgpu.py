@@ -55,7 +55,7 @@ class Stats(C.Structure):
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
            "asp_debug_state", "asp_debug_nogood", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
-           "asp_mlp_score"]
+           "asp_mlp_score", "asp_batch_create", "asp_batch_run", "asp_batch_info", "asp_batch_free"]
 
 
 def library_path() -> str:
@@ -85,6 +85,14 @@ def lib(build_if_missing: bool = True):
         L.asp_solve_async.restype = C.c_int
         L.asp_solve_batch.argtypes = [i32, vp, i64, vp, vp, vp, vp]
         L.asp_solve_batch.restype = C.c_int
+        L.asp_batch_create.argtypes = [i32, vp, i64, vp, i32, vp]
+        L.asp_batch_create.restype = C.c_int
+        L.asp_batch_run.argtypes = [vp, vp, vp, vp]
+        L.asp_batch_run.restype = C.c_int
+        L.asp_batch_info.argtypes = [vp, vp, vp, vp, vp]
+        L.asp_batch_info.restype = C.c_int
+        L.asp_batch_free.argtypes = [vp]
+        L.asp_batch_free.restype = None
         L.asp_stats.argtypes = [vp, vp]
         L.asp_stats.restype = C.c_int
         L.asp_free.argtypes = [vp]
@@ -289,6 +297,54 @@ def solve_batch(programs, max_models_each: int = 1, cap_each: int = 1):
                                  caps.ctypes.data))
     models = [words_to_models(b[:min(int(k), cap_each)], p.n_atoms) for b, k, p in zip(bufs, nm, programs)]
     return st, nm, models
+
+
+BATCH_AUTOTUNE = -1
+
+
+class BatchPlan:
+    """asp_batch_create: programs prepared for repeated batched solving
+    (descriptors uploaded, configuration chosen, launch captured in a CUDA
+    graph); run() replays it."""
+
+    def __init__(self, programs, max_models_each: int = 1, cap_each: int = 1, config: int = BATCH_AUTOTUNE):
+        self.programs = list(programs)
+        n = len(self.programs)
+        self.cap_each = cap_each
+        handles = (C.c_void_p * n)(*[p.handle.value for p in self.programs])
+        caps = np.full(n, cap_each, np.int64)
+        h = C.c_void_p()
+        _check(lib().asp_batch_create(n, handles, int(max_models_each), caps.ctypes.data, int(config), C.byref(h)))
+        self.handle = h
+        self._bufs = [np.zeros((max(cap_each, 1), max(p.words, 1)), np.uint64) for p in self.programs]
+        self._ptrs = (C.c_void_p * n)(*[b.ctypes.data for b in self._bufs])
+
+    def run(self):
+        n = len(self.programs)
+        st = np.zeros(n, np.int32)
+        nm = np.zeros(n, np.int64)
+        _check(lib().asp_batch_run(self.handle, st.ctypes.data, nm.ctypes.data, self._ptrs))
+        models = [words_to_models(b[:min(int(k), self.cap_each)], p.n_atoms)
+                  for b, k, p in zip(self._bufs, nm, self.programs)]
+        return st, nm, models
+
+    def info(self):
+        cfg, bt, grid = C.c_int32(), C.c_int32(), C.c_int32()
+        trial = (C.c_double * 2)()
+        _check(lib().asp_batch_info(self.handle, C.byref(cfg), C.byref(bt), C.byref(grid), trial))
+        return {"config": cfg.value, "block_threads": bt.value, "grid": grid.value,
+                "trial_ns_per_program": [trial[0], trial[1]]}
+
+    def close(self):
+        if self.handle:
+            lib().asp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def train_mlp(features: np.ndarray, labels: np.ndarray, weights: np.ndarray, epochs: int = 50,

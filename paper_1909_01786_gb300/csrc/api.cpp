@@ -16,8 +16,9 @@ cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st,
                          uint32_t passes);
-cudaError_t batch_configure(size_t smem, int *blocks_per_sm);
-cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
+int batch_threads(int config);
+cudaError_t batch_configure(int config, size_t smem, int *blocks_per_sm);
+cudaError_t launch_batch(int config, const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
                          size_t smem, cudaStream_t st);
 }  // namespace aspgpu
 
@@ -50,8 +51,10 @@ struct asp_prog {
     Dev D{};
     int grid = 1, block = 1024;
     size_t smem = 0;
-    Dev D1{};           // the same program as one CTA solves it in a batch
-    size_t smem1 = 0;
+    // the same program as one CTA solves it in a batch, for each batch
+    // kernel configuration (256 threads, 3 per SM; 128 threads, 6 per SM)
+    Dev D1[2]{};
+    size_t smem1[2] = {0, 0};
     int64_t n_nogoods = 0, n_literals = 0, n_units = 0, n_long = 0, store_bytes = 0;
     bool empty_nogood = false;
     // internal buffers for the blocking entry points
@@ -249,10 +252,12 @@ static int plan_grid(asp_prog *p, const HostStore &H)
 
 // Single-CTA layout of the program for batched solving: the whole store is
 // the CTA's range, and the view holds every atom and auxiliary variable if
-// they fit in the per-CTA shared-memory budget of the batch kernel.
-constexpr size_t BATCH_SMEM_BUDGET = 72 * 1024 - 1024;
+// they fit in the per-CTA shared-memory budget of the batch kernel
+// configuration (3 or 6 CTAs in an SM's 228 KB, less reserved and static
+// shared memory).
+constexpr size_t BATCH_SMEM_BUDGET[2] = {72 * 1024 - 1024, 34 * 1024};
 
-static int plan_batch(asp_prog *p, const HostStore &H)
+static int plan_batch(asp_prog *p, const HostStore &H, int config)
 {
     Dev D1 = p->D;
     std::vector<uint32_t> boff(32, 0), alo(1), an(1);
@@ -261,15 +266,115 @@ static int plan_batch(asp_prog *p, const HostStore &H)
     an[0] = 3 * D1.J;
     const size_t base = 8ull * D1.WW + 8ull * 32 + 4ull * 16 + MLP_SMEM_BYTES;
     D1.G = 1;
-    int rc = choose_view(p, H, D1, boff, alo, an, base, BATCH_SMEM_BUDGET);
+    int rc = choose_view(p, H, D1, boff, alo, an, base, BATCH_SMEM_BUDGET[config]);
     if (rc != ASP_OK) return rc;
     D1.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D1.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D1.cta_auxn = upload(p, an, rc);
-    p->D1 = D1;
-    p->smem1 = base + 4 * D1.view_words;
+    p->D1[config] = D1;
+    p->smem1[config] = base + 4 * D1.view_words;
     return rc;
 }
+
+// A batch prepared for repeated solving: per-program descriptors of the
+// chosen kernel configuration in device memory, and the launch (queue reset
+// + batch kernel) captured in a CUDA graph.
+struct asp_batch {
+    std::vector<asp_prog *> progs;
+    std::vector<int64_t> caps;
+    int64_t max_models_each = 0;
+    int config = 0, grid = 0;
+    size_t smem = 0;
+    double trial_ns[2] = {0.0, 0.0};
+    uint32_t queued = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// descriptors of programs `which` (indices into b->progs) for kernel
+// configuration `config`
+std::vector<Dev> batch_descriptors(const asp_batch *b, int config)
+{
+    std::vector<Dev> devs(b->progs.size());
+    for (size_t i = 0; i < b->progs.size(); i++) {
+        asp_prog *p = b->progs[i];
+        Dev d = p->D1[config];
+        d.mode = MODE_SOLVE;
+        d.max_models = b->max_models_each;
+        d.models_cap = b->caps[i];
+        d.models = p->d_models;
+        d.result = p->d_result;
+        d.conflict_budget = p->opt.conflict_budget;
+        d.time_budget_ns = p->opt.time_budget_ms > 0 ? p->opt.time_budget_ms * 1000000ll : 0;
+        devs[i] = d;
+    }
+    return devs;
+}
+
+// Upload the descriptors of configuration `config` and the queue `order`
+// (device scratch: descriptors | order | queue) and size the grid.
+int batch_prepare(asp_batch *b, int config, const std::vector<uint32_t> &order)
+{
+    const size_t n = b->progs.size();
+    size_t smem = 0;
+    for (asp_prog *p : b->progs) smem = std::max(smem, p->smem1[config]);
+    int per_sm = 0;
+    cudaError_t e = batch_configure(config, smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "batch configuration");
+    if (per_sm < 1) return fail(ASP_E_CUDA, "batch kernel cannot be resident");
+    const std::vector<Dev> devs = batch_descriptors(b, config);
+    Dev *d_devs = (Dev *)b->scratch;
+    uint32_t *d_order = (uint32_t *)((char *)b->scratch + sizeof(Dev) * n);
+    e = cudaMemcpyAsync(d_devs, devs.data(), sizeof(Dev) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);     // host vectors go out of scope
+    if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
+    b->config = config;
+    b->grid = (int)std::min<int64_t>((int64_t)b->progs[0]->n_sms * per_sm, (int64_t)order.size());
+    b->smem = smem;
+    b->queued = (uint32_t)order.size();
+    return ASP_OK;
+}
+
+// enqueue one batch launch as prepared: reset the queue counter, launch
+cudaError_t batch_enqueue(asp_batch *b)
+{
+    const size_t n = b->progs.size();
+    Dev *d_devs = (Dev *)b->scratch;
+    uint32_t *d_order = (uint32_t *)((char *)b->scratch + sizeof(Dev) * n);
+    unsigned int *d_queue = (unsigned int *)((char *)d_order + 4 * n);
+    cudaError_t e = cudaMemsetAsync(d_queue, 0, 64, b->stream);
+    if (e == cudaSuccess) e = launch_batch(b->config, d_devs, d_order, b->queued, d_queue, b->grid, b->smem, b->stream);
+    return e;
+}
+
+// autotuner trial: configuration `config` on the programs `sample`, device
+// time per program in ns (< 0 if the configuration cannot run)
+double batch_trial(asp_batch *b, int config, const std::vector<uint32_t> &sample)
+{
+    if (batch_prepare(b, config, sample) != ASP_OK) { g_err.clear(); return -1.0; }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    if (e == cudaSuccess) e = batch_enqueue(b);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) { cudaGetLastError(); return -1.0; }
+    return (double)ms * 1e6 / (double)sample.size();
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -410,7 +515,8 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     p->d_result = (long long *)alloc(sizeof(long long) * 4);
     p->d_sweep_acc = (Acc *)alloc(sizeof(Acc));
     if (rc == ASP_OK) rc = plan_grid(p, H);
-    if (rc == ASP_OK) rc = plan_batch(p, H);
+    if (rc == ASP_OK) rc = plan_batch(p, H, 0);
+    if (rc == ASP_OK) rc = plan_batch(p, H, 1);
     if (rc == ASP_OK) {
         cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(e, "load");
@@ -488,7 +594,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.ns_total = (int64_t)s.ns_total; o.ns_sweep = (int64_t)s.ns_sweep; o.ns_analysis = (int64_t)s.ns_analysis;
     o.ns_decision = (int64_t)s.ns_decision; o.ns_stability = (int64_t)s.ns_stab;
     o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
-    o.view_mode = D.view_mode; o.batch_view_mode = p->D1.view_mode;
+    o.view_mode = D.view_mode; o.batch_view_mode = p->D1[0].view_mode;
     o.ns_slowest_cta = (int64_t)s.ns_slowest; o.ns_slowest_sweep = (int64_t)s.ns_slowest_sweep;
 }
 
@@ -722,91 +828,151 @@ int asp_solve_batch(int32_t n, asp_prog *const *progs, int64_t max_models_each,
     g_err.clear();
     if (n < 0 || max_models_each < 0 || (n > 0 && (!progs || !statuses || !n_models))) return fail(ASP_E_ARG, "bad argument");
     if (n == 0) return ASP_OK;
+    asp_batch *b = nullptr;
+    int rc = asp_batch_create(n, progs, max_models_each, models_cap, 0, &b);
+    if (rc != ASP_OK) return rc;
+    rc = asp_batch_run(b, statuses, n_models, models);
+    std::string err = g_err;
+    asp_batch_free(b);
+    g_err = err;
+    return rc;
+}
+
+int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each, const int64_t *models_cap,
+                     int32_t config, asp_batch **out)
+{
+    g_err.clear();
+    if (!out) return fail(ASP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || max_models_each < 0 || !progs) return fail(ASP_E_ARG, "bad argument");
+    if (config < ASP_BATCH_AUTOTUNE || config > 1) return fail(ASP_E_ARG, "unknown batch configuration");
     for (int32_t i = 0; i < n; i++) {
         if (!progs[i]) return fail(ASP_E_ARG, "null program");
         if (progs[i]->stream != progs[0]->stream) return fail(ASP_E_ARG, "programs loaded on different streams");
-        if (models_cap && models_cap[i] > 0 && (!models || !models[i])) return fail(ASP_E_ARG, "null model buffer");
+        if (progs[i]->device != progs[0]->device) return fail(ASP_E_ARG, "programs loaded on different devices");
+        if (models_cap && models_cap[i] < 0) return fail(ASP_E_ARG, "negative model capacity");
     }
-    asp_prog *p0 = progs[0];
-    cudaStream_t st = p0->stream;
-    // per-program descriptors, largest store first in the queue
-    std::vector<Dev> devs(n);
-    std::vector<uint32_t> order(n);
-    size_t smem = 0;
+    asp_batch *b = new asp_batch;
+    b->progs.assign(progs, progs + n);
+    b->max_models_each = max_models_each;
+    b->caps.resize(n);
+    for (int32_t i = 0; i < n; i++) b->caps[i] = models_cap ? models_cap[i] : 0;
+    auto bail = [&](int rc) { asp_batch_free(b); return rc; };
+    // model buffers of every program
     for (int32_t i = 0; i < n; i++) {
         asp_prog *p = progs[i];
         const int64_t words = std::max<int64_t>(((int64_t)p->D.na + 63) / 64, 1);
-        const int64_t cap = models_cap ? models_cap[i] : 0;
-        const int64_t rows = std::max<int64_t>(cap, 1);
+        const int64_t rows = std::max<int64_t>(b->caps[i], 1);
         if (rows > p->d_models_rows) {
             void *q = dalloc(p, (size_t)(rows * words) * 8);
-            if (!q) return fail(ASP_E_OOM, "device allocation failed (models)");
+            if (!q) return bail(fail(ASP_E_OOM, "device allocation failed (models)"));
             p->d_models = (unsigned long long *)q;
             p->d_models_rows = rows;
         }
-        Dev d = p->D1;
-        d.mode = MODE_SOLVE;
-        d.max_models = max_models_each;
-        d.models_cap = cap;
-        d.models = p->d_models;
-        d.result = p->d_result;
-        d.conflict_budget = p->opt.conflict_budget;
-        d.time_budget_ns = p->opt.time_budget_ms > 0 ? p->opt.time_budget_ms * 1000000ll : 0;
-        devs[i] = d;
-        order[i] = (uint32_t)i;
-        smem = std::max(smem, p->smem1);
     }
+    // a stream that can be captured (the legacy default stream cannot)
+    b->stream = progs[0]->stream;
+    if (!b->stream) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { b->stream = nullptr; return bail(cuda_fail(e, "batch stream")); }
+        b->own_stream = true;
+    }
+    asp_prog *p0 = progs[0];
+    b->scratch_bytes = sizeof(Dev) * (size_t)n + 4 * (size_t)n + 64;
+    if (p0->opt.dev_alloc) b->scratch = p0->opt.dev_alloc(b->scratch_bytes, p0->opt.alloc_ctx);
+    else if (cudaMalloc(&b->scratch, b->scratch_bytes) != cudaSuccess) { cudaGetLastError(); b->scratch = nullptr; }
+    if (!b->scratch) return bail(fail(ASP_E_OOM, "device allocation failed (batch descriptors)"));
+    // queue order: largest store first
+    std::vector<uint32_t> order(n);
+    for (int32_t i = 0; i < n; i++) order[i] = (uint32_t)i;
     std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t a, uint32_t b) { return progs[a]->n_literals > progs[b]->n_literals; });
-    // per-call device scratch: descriptors, queue order, queue counter
-    const size_t bytes = sizeof(Dev) * (size_t)n + 4 * (size_t)n + 64;
-    void *scratch = nullptr;
-    if (p0->opt.dev_alloc) scratch = p0->opt.dev_alloc(bytes, p0->opt.alloc_ctx);
-    else if (cudaMalloc(&scratch, bytes) != cudaSuccess) { cudaGetLastError(); scratch = nullptr; }
-    if (!scratch) return fail(ASP_E_OOM, "device allocation failed (batch descriptors)");
-    auto release = [&]() {
-        if (p0->opt.dev_free) p0->opt.dev_free(scratch, bytes, p0->opt.alloc_ctx);
-        else cudaFree(scratch);
-    };
-    Dev *d_devs = (Dev *)scratch;
-    uint32_t *d_order = (uint32_t *)((char *)scratch + sizeof(Dev) * (size_t)n);
-    unsigned int *d_queue = (unsigned int *)((char *)d_order + 4 * (size_t)n);
-    int rc = ASP_OK;
-    int per_sm = 0;
-    cudaError_t e = cudaMemcpyAsync(d_devs, devs.data(), sizeof(Dev) * (size_t)n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, 64, st);
-    if (e == cudaSuccess) e = batch_configure(smem, &per_sm);
-    if (e == cudaSuccess && per_sm < 1) { rc = fail(ASP_E_CUDA, "batch kernel cannot be resident"); }
-    if (e == cudaSuccess && rc == ASP_OK) {
-        int grid = (int)std::min<int64_t>((int64_t)p0->n_sms * per_sm, n);
-        e = launch_batch(d_devs, d_order, (uint32_t)n, d_queue, grid, smem, st);
+                     [&](uint32_t a, uint32_t c) { return progs[a]->n_literals > progs[c]->n_literals; });
+    int chosen = config < 0 ? 0 : config;
+    if (config == ASP_BATCH_AUTOTUNE) {
+        // each configuration solves the same sample (up to 512 programs spread
+        // over the queue order) once; the lower device time per program wins
+        const size_t S = std::min<size_t>((size_t)n, 512);
+        std::vector<uint32_t> sample(S);
+        for (size_t k = 0; k < S; k++) sample[k] = order[k * (size_t)n / S];
+        double best = -1.0;
+        for (int c = 0; c < 2; c++) {
+            b->trial_ns[c] = batch_trial(b, c, sample);
+            if (b->trial_ns[c] >= 0.0 && (best < 0.0 || b->trial_ns[c] < best)) { best = b->trial_ns[c]; chosen = c; }
+        }
+        if (best < 0.0) return bail(fail(ASP_E_CUDA, "no batch configuration can run"));
     }
-    if (e == cudaSuccess && rc == ASP_OK) e = st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize();
-    if (e != cudaSuccess && rc == ASP_OK) rc = cuda_fail(e, "batch solve");
+    int rc = batch_prepare(b, chosen, order);
+    if (rc != ASP_OK) return bail(rc);
+    // capture queue reset + launch once; every asp_batch_run replays it
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = batch_enqueue(b);
+        e = cudaStreamEndCapture(b->stream, &b->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "batch graph"));
+    *out = b;
+    return ASP_OK;
+}
+
+int asp_batch_run(asp_batch *b, int32_t *statuses, int64_t *n_models, uint64_t *const *models)
+{
+    g_err.clear();
+    if (!b || !statuses || !n_models) return fail(ASP_E_ARG, "bad argument");
+    const int32_t n = (int32_t)b->progs.size();
+    for (int32_t i = 0; i < n; i++)
+        if (b->caps[i] > 0 && (!models || !models[i])) return fail(ASP_E_ARG, "null model buffer");
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch solve");
     bool device_error = false, capacity = false;
-    for (int32_t i = 0; i < n && rc == ASP_OK; i++) {
-        asp_prog *p = progs[i];
+    for (int32_t i = 0; i < n; i++) {
+        asp_prog *p = b->progs[i];
         long long res[4];
         e = cudaMemcpy(res, p->d_result, sizeof(res), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "batch result"); break; }
+        if (e != cudaSuccess) return cuda_fail(e, "batch result");
         statuses[i] = (int32_t)res[0];
         n_models[i] = res[1];
         device_error |= res[2] != 0;
-        const int64_t cap = models_cap ? models_cap[i] : 0;
+        const int64_t cap = b->caps[i];
         const int64_t words = ((int64_t)p->D.na + 63) / 64;
         const int64_t copy = std::min<int64_t>(res[1], cap);
         capacity |= res[1] > cap && cap > 0;
         if (copy > 0 && words > 0) {
             e = cudaMemcpy(models[i], p->d_models, (size_t)(copy * words) * 8, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "batch models"); break; }
+            if (e != cudaSuccess) return cuda_fail(e, "batch models");
         }
     }
-    release();
-    if (rc != ASP_OK) return rc;
     if (device_error) return fail(ASP_E_DEVICE, "device-side error in some program (learned store full)");
     if (capacity) return fail(ASP_E_CAPACITY, "more answer sets than model buffer rows for some program");
     return ASP_OK;
+}
+
+int asp_batch_info(const asp_batch *b, int32_t *config, int32_t *block_threads, int32_t *grid, double *trial_ns)
+{
+    if (!b) return fail(ASP_E_ARG, "bad argument");
+    if (config) *config = b->config;
+    if (block_threads) *block_threads = batch_threads(b->config);
+    if (grid) *grid = b->grid;
+    if (trial_ns) { trial_ns[0] = b->trial_ns[0]; trial_ns[1] = b->trial_ns[1]; }
+    return ASP_OK;
+}
+
+void asp_batch_free(asp_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->scratch) {
+        asp_prog *p0 = b->progs[0];
+        if (p0->opt.dev_free) p0->opt.dev_free(b->scratch, b->scratch_bytes, p0->opt.alloc_ctx);
+        else cudaFree(b->scratch);
+    }
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // extern "C"

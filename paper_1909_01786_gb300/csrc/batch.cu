@@ -7,8 +7,9 @@ namespace aspgpu {
 // Batched solving: each CTA takes programs from a queue (the host orders it
 // largest first) and solves each alone, with the whole program's assignment
 // view in its shared memory and a CTA barrier as the phase barrier.
-__global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
-                                                       unsigned int *queue)
+template <int THREADS, int MIN_BLOCKS>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
+                                                                    unsigned int *queue)
 {
     extern __shared__ unsigned long long smem_raw[];
     __shared__ Dev sD;
@@ -49,17 +50,29 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const Dev *devs, const ui
     }
 }
 
-cudaError_t batch_configure(size_t smem, int *blocks_per_sm)
+// Batch kernel configurations the autotuner chooses from: threads per CTA
+// and the CTAs per SM the register budget is compiled for.
+//   0: 256 threads, 3 per SM (programs up to ~70 KB of view)
+//   1: 128 threads, 6 per SM (twice the programs in flight, ~34 KB views)
+int batch_threads(int config) { return config == 1 ? 128 : 256; }
+
+cudaError_t batch_configure(int config, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    if (config == 1) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<128, 6>, 128, smem);
+    }
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<256, 3>, 256, smem);
 }
 
-cudaError_t launch_batch(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
-                         size_t smem, cudaStream_t st)
+cudaError_t launch_batch(int config, const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue,
+                         int grid, size_t smem, cudaStream_t st)
 {
-    batch_kernel<<<grid, 256, smem, st>>>(devs, order, n, queue);
+    if (config == 1) batch_kernel<128, 6><<<grid, 128, smem, st>>>(devs, order, n, queue);
+    else batch_kernel<256, 3><<<grid, 256, smem, st>>>(devs, order, n, queue);
     return cudaGetLastError();
 }
 

@@ -77,3 +77,41 @@ def test_batch_equals_single_program_solves(gpu):
         assert st[i] in (gpu.SAT, gpu.UNSAT)
         for m in models[i]:
             assert oracle.is_answer_set(p, m)
+
+
+@pytest.mark.parametrize("config", [0, 1])
+def test_batch_plan_configurations_and_replays(gpu, config):
+    """A prepared batch (descriptors uploaded, launch captured in a CUDA
+    graph) solved twice with either kernel configuration: full enumeration
+    equals brute force both times."""
+    progs = [tiny_program(i) for i in range(5, 400, 17)]
+    P = [gpu.Program(p) for p in progs]
+    plan = gpu.BatchPlan(P, max_models_each=0, cap_each=4096, config=config)
+    assert plan.info()["config"] == config
+    assert plan.info()["block_threads"] == (256 if config == 0 else 128)
+    for _ in range(2):
+        st, nm, models = plan.run()
+        for i, p in enumerate(progs):
+            want = _sets(oracle.brute_force(p))
+            assert _sets(models[i]) == want and nm[i] == len(want), i
+            assert st[i] == (gpu.SAT if want else gpu.UNSAT)
+    plan.close()
+
+
+def test_autotuned_batch_matches_the_oracle(gpu):
+    progs = batch_programs(40, rules_per_atom=2, lo=50, hi=2000, config_id=404)
+    P = [gpu.Program(p, time_budget_ms=20_000) for p in progs]
+    plan = gpu.BatchPlan(P, max_models_each=1, cap_each=1)
+    info = plan.info()
+    assert info["config"] in (0, 1)
+    t0, t1 = info["trial_ns_per_program"]
+    assert t0 > 0 and t1 > 0
+    assert info["trial_ns_per_program"][info["config"]] == min(t0, t1)
+    st, nm, models = plan.run()
+    for i, p in enumerate(progs):
+        ost, _, _ = oracle.cdnl(p, max_models=1, time_budget_s=30)
+        assert ost in (oracle.SAT, oracle.UNSAT)
+        assert st[i] == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT), i
+        for m in models[i]:
+            assert oracle.is_answer_set(p, m)
+    plan.close()
