@@ -409,12 +409,14 @@ def _learned(a, aspgpu, torch):
     t0 = time.perf_counter()
     X, y = H.collect_traces(_a11_programs(a.learned_train, 10**6), conflict_budget=budget)
     w, tstats = H.fit(X, y)
+    ws, sstats = H.fit(X, y, static=True)
     t_train = time.perf_counter() - t0
     H.save(w, os.path.join(ROOT, "gpurun_out", "heuristic_mlp.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
            else os.devnull, **tstats)
     evalp = _a11_programs(a.learned, 2 * 10**6)
     out = {}
-    for name, kw in (("plain", dict(heuristic=0)), ("learned", dict(heuristic=2, mlp_weights=w))):
+    for name, kw in (("plain", dict(heuristic=0)), ("learned", dict(heuristic=2, mlp_weights=w)),
+                     ("learned_static", dict(heuristic=3, mlp_weights=ws))):
         P = [aspgpu.Program(p, conflict_budget=budget, time_budget_ms=20_000, deps_levels=1024,
                             learned_capacity=1 << 20, **kw) for p in evalp]
         torch.cuda.synchronize()
@@ -431,23 +433,29 @@ def _learned(a, aspgpu, torch):
             q.close()
     # zero mismatches: where both decided they agree; models are answer sets
     import oracle
-    sp, sl = out["plain"]["statuses"], out["learned"]["statuses"]
-    both = ((sp == 10) | (sp == 20)) & ((sl == 10) | (sl == 20))
-    mism = int((sp[both] != sl[both]).sum())
+    sp = out["plain"]["statuses"]
+    mism = 0
+    for name in ("learned", "learned_static"):
+        sl = out[name]["statuses"]
+        both = ((sp == 10) | (sp == 20)) & ((sl == 10) | (sl == 20))
+        mism += int((sp[both] != sl[both]).sum())
     checked = bad = 0
-    for name in ("plain", "learned"):
+    for name in ("plain", "learned", "learned_static"):
         for i, m in enumerate(out[name]["models"]):
             if len(m):
                 checked += 1
                 bad += not oracle.is_answer_set(evalp[i], m[0])
-    for name in ("plain", "learned"):
+    for name in ("plain", "learned", "learned_static"):
         del out[name]["statuses"], out[name]["models"]
     return {"workload": f"{a.learned} held-out programs (half random, 4 rules per atom, 200-2000 atoms; "
                         f"half 3-colourings, 40-400 vertices), conflict budget {budget}, batched",
             "training": {"programs": a.learned_train, "seconds": t_train, **tstats},
             **out, "status_mismatches": mism, "models_checked": checked, "invalid_models": bad,
             "speedup_solved_per_s": (out["learned"]["solved_per_s"] / out["plain"]["solved_per_s"])
-            if out["plain"]["solved"] else None}
+            if out["plain"]["solved"] else None,
+            "speedup_static_solved_per_s": (out["learned_static"]["solved_per_s"] / out["plain"]["solved_per_s"])
+            if out["plain"]["solved"] else None,
+            "static_training": sstats}
 
 
 def run_sweeps(a):

@@ -55,6 +55,9 @@ extern "C" {
 #define ASP_HEUR_OCCURRENCE 0 /* static: occurrence count of the head (Section 4) */
 #define ASP_HEUR_ACTIVITY 1   /* occurrence count plus activity bumped by conflicts */
 #define ASP_HEUR_LEARNED 2    /* log1p(head occurrences) + log sigmoid(MLP logit) (not in the paper) */
+#define ASP_HEUR_LEARNED_STATIC 3 /* the same score computed once per rule at load, with the
+                                     search-state features at their values before the first
+                                     decision: a learned static rule order (not in the paper) */
 
 /* Shared-memory assignment view of each CTA during the propagate-and-check
  * sweep (Section 4.1; the layout is this implementation's, not the paper's).
@@ -89,7 +92,7 @@ typedef struct {
     void (*dev_free)(void *ptr, size_t bytes, void *ctx);
     void *alloc_ctx;
     /* learned heuristic: ASP_MLP_PARAMS host floats, copied at load (used
-       when heuristic = ASP_HEUR_LEARNED; stored as bf16) */
+       when heuristic = ASP_HEUR_LEARNED or ASP_HEUR_LEARNED_STATIC; stored as bf16) */
     const float *mlp_weights;
     /* record up to this many decisions per solve for asp_trace; 0 = none */
     int64_t trace_capacity;

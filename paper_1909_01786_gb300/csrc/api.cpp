@@ -17,6 +17,7 @@ cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStr
 cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st,
                          uint32_t passes);
 int batch_threads(int config);
+int mlp_prior(const uint16_t *d_w, const std::vector<float> &features, int64_t n, float *d_out, cudaStream_t st);
 cudaError_t batch_configure(int config, size_t smem, int *blocks_per_sm);
 cudaError_t launch_batch(int config, const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
                          size_t smem, cudaStream_t st);
@@ -449,7 +450,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.WW = WW;
     D.Wlevels = WW * 64u;
     D.heuristic = (uint32_t)std::max(0, p->opt.heuristic);
-    if (D.heuristic > 2) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
+    if (D.heuristic > 3) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
     p->n_nogoods = H.n_nogoods;
     p->n_literals = H.n_literals;
     p->n_units = (int64_t)H.units.size();
@@ -474,7 +475,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     if (rc == ASP_OK) D.rneg = upload(p, H.rneg, rc);
     if (rc == ASP_OK) D.score = upload(p, H.score, rc);
     if (rc == ASP_OK) D.rfeat = upload(p, H.rfeat, rc);
-    if (rc == ASP_OK && D.heuristic == 2) {
+    if (rc == ASP_OK && D.heuristic >= 2) {
         if (!p->opt.mlp_weights) rc = fail(ASP_E_ARG, "learned heuristic without mlp_weights");
         else {
             // bf16 by round-to-nearest-even of the float bits
@@ -486,6 +487,22 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
             }
             D.mlp = upload(p, w, rc);
         }
+    }
+    if (rc == ASP_OK && D.heuristic == 3) {
+        // the search-state features at their values before the first
+        // decision: activity 0, every negative body atom unassigned, none
+        // false, level 1, no conflicts, empty trail
+        std::vector<float> X((size_t)D.J * N_FEATURES, 0.0f);
+        for (uint32_t j = 0; j < D.J; j++) {
+            float *x = X.data() + (size_t)j * N_FEATURES;
+            for (int q = 0; q < RULE_STATIC_FEATURES; q++) x[q] = H.rfeat[(size_t)j * RULE_STATIC_FEATURES + q];
+            x[9] = (float)(H.rneg_off[j + 1] - H.rneg_off[j]);
+            x[11] = 1.0f / 64.0f;
+        }
+        float *prior = (float *)dalloc(p, (size_t)D.J * sizeof(float) + 4);
+        if (!prior) rc = fail(ASP_E_OOM, "device allocation failed (prior)");
+        else rc = mlp_prior(D.mlp, X, (int64_t)D.J, prior, p->stream);
+        D.prior = prior;
     }
     if (rc == ASP_OK && p->opt.trace_capacity > 0) {
         D.trace_cap = (uint32_t)std::min<int64_t>(p->opt.trace_capacity, 1 << 24);

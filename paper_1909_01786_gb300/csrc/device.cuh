@@ -128,6 +128,7 @@ struct Dev {
     // [J][8], MLP weights (bf16 bits, MLP_PARAMS), decision trace
     const float *rfeat;
     const uint16_t *mlp;
+    const float *prior;       // heuristic 3: per-rule score computed at load
     uint32_t *trace;          // [trace_cap][TRACE_WORDS]
     uint32_t trace_cap, pad3;
     uint32_t *asg;

@@ -107,7 +107,43 @@ __global__ void mlp_score_kernel(const uint16_t *Wb, const float *X, int n, floa
     }
 }
 
+// Static prior of heuristic 3: feature 0 + log sigmoid(MLP) per row.
+__global__ void mlp_prior_kernel(const uint16_t *Wb, const float *X, int n, float *out)
+{
+    __shared__ __nv_bfloat16 w[MLP_PARAMS];
+    for (int p = threadIdx.x; p < MLP_PARAMS; p += blockDim.x) w[p] = __ushort_as_bfloat16(Wb[p]);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float x[N_FEATURES];
+#pragma unroll
+        for (int q = 0; q < N_FEATURES; q++) x[q] = X[(size_t)i * N_FEATURES + q];
+        const float z = mlp_score(w, x);
+        const float log_p = z >= 0.0f ? -log1pf(__expf(-z)) : z - log1pf(__expf(z));
+        out[i] = x[0] + log_p;
+    }
+}
+
 }  // namespace
+
+// Per-rule prior of heuristic 3 on the device: features uploaded from the
+// host, bf16 weights already on the device, result left in d_out.
+int mlp_prior(const uint16_t *d_w, const std::vector<float> &features, int64_t n, float *d_out, cudaStream_t st)
+{
+    if (n <= 0) return ASP_OK;
+    float *dX = nullptr;
+    const size_t bx = (size_t)n * N_FEATURES * sizeof(float);
+    if (cudaMalloc(&dX, bx) != cudaSuccess) { cudaGetLastError(); return internal_fail(ASP_E_OOM, "device allocation failed (prior)"); }
+    cudaError_t e = cudaMemcpyAsync(dX, features.data(), bx, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        mlp_prior_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(d_w, dX, (int)n, d_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dX);
+    if (e != cudaSuccess) return internal_fail(ASP_E_CUDA, cudaGetErrorString(e));
+    return ASP_OK;
+}
+
 }  // namespace aspgpu
 
 extern "C" int asp_mlp_score(const float *weights, const float *features, int64_t n, float *scores)

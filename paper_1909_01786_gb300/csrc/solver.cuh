@@ -941,7 +941,9 @@ __device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, ui
                     }
                 }
             }
-            if (D.heuristic == 2) {
+            if (D.heuristic == 3) {
+                key = ((unsigned long long)float_key(__ldg(D.prior + j)) << 32) | (0xFFFFFFFFull - j);
+            } else if (D.heuristic == 2) {
                 // plain score (log1p occurrences of the head, feature 0) plus
                 // the log of the learned probability that the rule's body
                 // holds in an answer set

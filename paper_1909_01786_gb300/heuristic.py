@@ -11,7 +11,12 @@
 3. The solver (heuristic = ASP_HEUR_LEARNED) chooses the applicable rule with
    the largest log1p(occurrences of its head) + log P(body holds in an answer
    set): the plain heuristic's impact estimate weighted by the learned
-   probability that the choice is right.
+   probability that the choice is right.  With ASP_HEUR_LEARNED_STATIC the
+   score is computed once per rule when the program is loaded, with the
+   search-state features at their values before the first decision; the
+   model for it is trained with those features held at the same values
+   (fit(..., static=True)), so it learns a rule order from the program's
+   structure alone and costs nothing per decision.
 
 Propagation, learning and the stability check are untouched, so answer sets
 and SAT/UNSAT answers do not depend on the weights; only the search order
@@ -64,9 +69,26 @@ def collect_traces(programs, conflict_budget: int = 200, trace_capacity: int = 4
         np.concatenate(y).astype(np.float32) if y else np.zeros(0, np.float32)
 
 
-def fit(X: np.ndarray, y: np.ndarray, epochs: int = 60, learning_rate: float = 0.05, seed: int = 0):
+def static_features(X: np.ndarray) -> np.ndarray:
+    """The features a rule has before the first decision (what the solver
+    uses for ASP_HEUR_LEARNED_STATIC): activity 0, every negative body atom
+    unassigned (feature 2 = |B-|), none false, level 1, no conflicts, empty
+    trail."""
+    Z = np.array(X, np.float32, copy=True)
+    Z[:, 8] = 0.0
+    Z[:, 9] = Z[:, 2]
+    Z[:, 10] = 0.0
+    Z[:, 11] = 1.0 / 64.0
+    Z[:, 12:] = 0.0
+    return Z
+
+
+def fit(X: np.ndarray, y: np.ndarray, epochs: int = 60, learning_rate: float = 0.05, seed: int = 0,
+        static: bool = False):
     """Train on standardised features, return weights for raw features and
-    the training statistics."""
+    the training statistics.  static: train on static_features(X)."""
+    if static:
+        X = static_features(X)
     mu = X.mean(0)
     sd = X.std(0)
     sd[sd < 1e-6] = 1.0

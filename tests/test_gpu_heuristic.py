@@ -120,3 +120,33 @@ def test_learned_heuristic_sat_agreement(gpu, seed):
     assert st == (aspgpu.SAT if ost == oracle.SAT else aspgpu.UNSAT)
     for m in models:
         assert oracle.is_answer_set(prog, m)
+
+
+@pytest.mark.parametrize("index", list(range(3, 200, 29)))
+def test_static_learned_order_leaves_answer_sets_unchanged(gpu, index):
+    aspgpu, H = gpu
+    prog = tiny_program(index)
+    want = {frozenset(np.nonzero(m)[0].tolist()) for m in oracle.brute_force(prog)}
+    _, models, n = aspgpu.Program(prog, heuristic=3, mlp_weights=H.init_weights(index)).solve(0, cap=4096)
+    assert {frozenset(np.nonzero(m)[0].tolist()) for m in models} == want and n == len(want)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_static_learned_order_sat_agreement(gpu, seed):
+    aspgpu, H = gpu
+    prog = random_program(600, 1200, program_seed(503, seed))
+    ost, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=30)
+    assert ost in (oracle.SAT, oracle.UNSAT)
+    st, models, _ = aspgpu.Program(prog, heuristic=3, mlp_weights=H.init_weights(seed),
+                                   time_budget_ms=30_000).solve(1, cap=1)
+    assert st == (aspgpu.SAT if ost == oracle.SAT else aspgpu.UNSAT)
+    for m in models:
+        assert oracle.is_answer_set(prog, m)
+
+
+def test_static_features_hold_the_search_state_at_its_start(gpu):
+    aspgpu, H = gpu
+    X = np.random.default_rng(3).normal(0, 1, (50, 16)).astype(np.float32)
+    Z = H.static_features(X)
+    assert (Z[:, :8] == X[:, :8]).all() and (Z[:, 9] == X[:, 2]).all()
+    assert (Z[:, [8, 10, 12, 13, 14, 15]] == 0).all() and np.allclose(Z[:, 11], 1 / 64)
