@@ -48,6 +48,7 @@ def _args():
     ap.add_argument("--rules", type=int, default=400_000)
     ap.add_argument("--conflicts", type=int, default=200, help="conflict budget per step")
     ap.add_argument("--view", type=int, default=0, help="sweep view layout: 0 auto, 1 plain, 2 packed, 3 bytes")
+    ap.add_argument("--frontier", action="store_true", help="frontier rounds (full sweeps after backjumps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample length")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -198,7 +199,7 @@ def run_ours(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     prog = _program(a)
-    P = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000, view_mode=a.view)
+    P = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000, view_mode=a.view, frontier=a.frontier)
     words = max((prog.n_atoms + 63) // 64, 1)
     d_models = torch.zeros(words, dtype=torch.int64, device=dev)
     d_result = torch.zeros(4, dtype=torch.int64, device=dev)
@@ -299,7 +300,7 @@ def run_ours(a, rank, world, local_rank):
             for _ in range(n_e2e):
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
-                Q = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000, view_mode=a.view)
+                Q = aspgpu.Program(prog, conflict_budget=a.conflicts, time_budget_ms=120_000, view_mode=a.view, frontier=a.frontier)
                 Q.solve(1, cap=1)
                 s = Q.stats()
                 Q.close()

@@ -99,7 +99,11 @@ typedef struct {
     /* ASP_VIEW_*: the widest view allowed (a wider one than fits in shared
        memory falls back to the next narrower); 0 = ASP_VIEW_AUTO */
     int32_t view_mode;
-    int32_t reserved0;
+    /* 1: frontier propagation -- a round checks only the nogoods of the
+       variables assigned in the previous round (Algorithm 2's frontier;
+       nogood-by-variable occurrence lists built at load), full sweeps after
+       backjumps; 0: every round sweeps every nogood */
+    int32_t frontier;
 } asp_options;
 
 typedef struct {
@@ -170,9 +174,9 @@ typedef struct asp_batch asp_batch;
  * launch (queue reset + batch kernel) in a CUDA graph.  Configurations:
  * 0 = 256 threads per CTA, 3 CTAs per SM; 1 = 128 threads, 6 per SM (twice
  * the programs in flight, smaller shared-memory views).  config =
- * ASP_BATCH_AUTOTUNE runs each configuration once on a sample of up to 512
- * programs spread over the queue and keeps the one with the lower device
- * time per program (the trial solves change nothing but the programs' last
+ * ASP_BATCH_AUTOTUNE runs each configuration once on a sample of up to 256
+ * programs spread over the queue (each with at most 32 conflicts and 2 s of
+ * device time) and keeps the one with the lower device time per program (the trial solves change nothing but the programs' last
  * results).  models_cap may be NULL (no models kept).  The programs must
  * stay loaded until asp_batch_free.  Errors: ASP_E_ARG, ASP_E_OOM,
  * ASP_E_CUDA. */

@@ -39,7 +39,7 @@ class Options(C.Structure):
                 ("block_threads", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
                 ("mlp_weights", C.c_void_p), ("trace_capacity", C.c_int64),
-                ("view_mode", C.c_int32), ("reserved0", C.c_int32)]
+                ("view_mode", C.c_int32), ("frontier", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -157,7 +157,7 @@ class Program:
 
     def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
                  learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True,
-                 mlp_weights=None, trace_capacity=0, view_mode=0):
+                 mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False):
         L = lib()
         self.n_atoms = int(prog.n_atoms)
         self._keep = []
@@ -170,6 +170,7 @@ class Program:
             opt.mlp_weights = w.ctypes.data
         opt.trace_capacity = int(trace_capacity)
         opt.view_mode = int(view_mode)
+        opt.frontier = 1 if frontier else 0
         opt.heuristic, opt.deps_levels = heuristic, deps_levels
         opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
         opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads

@@ -298,9 +298,14 @@ struct asp_batch {
 
 namespace {
 
-// descriptors of programs `which` (indices into b->progs) for kernel
-// configuration `config`
-std::vector<Dev> batch_descriptors(const asp_batch *b, int config)
+// autotuner trials solve each sampled program with at most this many
+// conflicts and this much device time (the same short work for every
+// configuration)
+constexpr long long TRIAL_CONFLICTS = 32, TRIAL_TIME_NS = 2000000000ll;
+
+// descriptors of every program of the batch for kernel configuration
+// `config` (trial: the autotuner's shortened budgets)
+std::vector<Dev> batch_descriptors(const asp_batch *b, int config, bool trial = false)
 {
     std::vector<Dev> devs(b->progs.size());
     for (size_t i = 0; i < b->progs.size(); i++) {
@@ -313,6 +318,11 @@ std::vector<Dev> batch_descriptors(const asp_batch *b, int config)
         d.result = p->d_result;
         d.conflict_budget = p->opt.conflict_budget;
         d.time_budget_ns = p->opt.time_budget_ms > 0 ? p->opt.time_budget_ms * 1000000ll : 0;
+        if (trial) {
+            d.conflict_budget = d.conflict_budget > 0 ? std::min(d.conflict_budget, TRIAL_CONFLICTS) : TRIAL_CONFLICTS;
+            d.time_budget_ns = d.time_budget_ns > 0 ? std::min(d.time_budget_ns, TRIAL_TIME_NS) : TRIAL_TIME_NS;
+            d.max_models = 1;
+        }
         devs[i] = d;
     }
     return devs;
@@ -320,7 +330,7 @@ std::vector<Dev> batch_descriptors(const asp_batch *b, int config)
 
 // Upload the descriptors of configuration `config` and the queue `order`
 // (device scratch: descriptors | order | queue) and size the grid.
-int batch_prepare(asp_batch *b, int config, const std::vector<uint32_t> &order)
+int batch_prepare(asp_batch *b, int config, const std::vector<uint32_t> &order, bool trial = false)
 {
     const size_t n = b->progs.size();
     size_t smem = 0;
@@ -329,7 +339,7 @@ int batch_prepare(asp_batch *b, int config, const std::vector<uint32_t> &order)
     cudaError_t e = batch_configure(config, smem, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "batch configuration");
     if (per_sm < 1) return fail(ASP_E_CUDA, "batch kernel cannot be resident");
-    const std::vector<Dev> devs = batch_descriptors(b, config);
+    const std::vector<Dev> devs = batch_descriptors(b, config, trial);
     Dev *d_devs = (Dev *)b->scratch;
     uint32_t *d_order = (uint32_t *)((char *)b->scratch + sizeof(Dev) * n);
     e = cudaMemcpyAsync(d_devs, devs.data(), sizeof(Dev) * n, cudaMemcpyHostToDevice, b->stream);
@@ -359,7 +369,7 @@ cudaError_t batch_enqueue(asp_batch *b)
 // time per program in ns (< 0 if the configuration cannot run)
 double batch_trial(asp_batch *b, int config, const std::vector<uint32_t> &sample)
 {
-    if (batch_prepare(b, config, sample) != ASP_OK) { g_err.clear(); return -1.0; }
+    if (batch_prepare(b, config, sample, true) != ASP_OK) { g_err.clear(); return -1.0; }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms = 0.0f;
     cudaError_t e = cudaEventCreate(&e0);
@@ -531,6 +541,25 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.bar = (Barrier *)alloc(sizeof(Barrier));
     p->d_result = (long long *)alloc(sizeof(long long) * 4);
     p->d_sweep_acc = (Acc *)alloc(sizeof(Acc));
+    if (rc == ASP_OK && p->opt.frontier) {
+        // per variable, the ids of the bucket nogoods it occurs in
+        std::vector<uint32_t> off((size_t)D.nv + 1, 0), occ;
+        for (int L = 2; L <= BUCKET_MAX; L++) {
+            const std::vector<uint32_t> &rows = H.bucket_rows[L];
+            for (size_t t = 0; t < rows.size(); t++) off[(rows[t] >> 1) + 1]++;
+        }
+        for (uint32_t v = 0; v < D.nv; v++) off[v + 1] += off[v];
+        occ.resize(off[D.nv]);
+        std::vector<uint32_t> fill(off.begin(), off.end() - 1);
+        for (int L = 2; L <= BUCKET_MAX; L++) {
+            const std::vector<uint32_t> &rows = H.bucket_rows[L];
+            for (size_t t = 0; t < rows.size(); t++)
+                occ[fill[rows[t] >> 1]++] = bucket_nogood_id((uint32_t)L, (uint32_t)(t / (size_t)L));
+        }
+        D.frontier = 1;
+        D.occ_off = upload(p, off, rc);
+        if (rc == ASP_OK) D.occ = upload(p, occ, rc);
+    }
     if (rc == ASP_OK) rc = plan_grid(p, H);
     if (rc == ASP_OK) rc = plan_batch(p, H, 0);
     if (rc == ASP_OK) rc = plan_batch(p, H, 1);
@@ -907,9 +936,10 @@ int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each,
                      [&](uint32_t a, uint32_t c) { return progs[a]->n_literals > progs[c]->n_literals; });
     int chosen = config < 0 ? 0 : config;
     if (config == ASP_BATCH_AUTOTUNE) {
-        // each configuration solves the same sample (up to 512 programs spread
-        // over the queue order) once; the lower device time per program wins
-        const size_t S = std::min<size_t>((size_t)n, 512);
+        // each configuration solves the same sample (up to 256 programs spread
+        // over the queue order, at most 32 conflicts and 2 s each) once; the
+        // lower device time per program wins
+        const size_t S = std::min<size_t>((size_t)n, 256);
         std::vector<uint32_t> sample(S);
         for (size_t k = 0; k < S; k++) sample[k] = order[k * (size_t)n / S];
         double best = -1.0;

@@ -63,7 +63,8 @@ struct Ctl {              // double-buffered control block (phase parity)
     uint32_t n_learned, lfill, stab_first, trace_n;
     long long n_models;
     int32_t status, err;
-    int32_t conflict, pad;
+    int32_t conflict;
+    uint32_t full;              // the next round sweeps every nogood (else the frontier)
 };
 
 struct Acc {              // per-phase accumulators, indexed by phase % 4
@@ -130,7 +131,13 @@ struct Dev {
     const uint16_t *mlp;
     const float *prior;       // heuristic 3: per-rule score computed at load
     uint32_t *trace;          // [trace_cap][TRACE_WORDS]
-    uint32_t trace_cap, pad3;
+    uint32_t trace_cap;
+    // frontier propagation (Algorithm 2's idea): a round checks only the
+    // bucket nogoods of the variables assigned in the previous round, found
+    // through occ_off/occ (per variable, the ids of the bucket nogoods it
+    // occurs in); full sweeps after (re)starts and backjumps
+    uint32_t frontier;
+    const uint32_t *occ_off, *occ;
     uint32_t *asg;
     int32_t *dl;
     uint32_t *reason;

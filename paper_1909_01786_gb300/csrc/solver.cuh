@@ -446,6 +446,33 @@ __device__ __forceinline__ void warp_deps(const SweepCtx &X, const uint32_t (&va
     }
 }
 
+// warp_deps for a nogood of L <= BUCKET_MAX literals known at run time
+// (var[q] for q < L).  All 32 lanes call it with the same arguments.
+__device__ __forceinline__ void warp_deps_dyn(const SweepCtx &X, const uint32_t (&var)[BUCKET_MAX], uint32_t L,
+                                              uint32_t x)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nw = deps_words(D, X.cdl);
+    const uint32_t dbit = level_bit(D, X.cdl);
+    int32_t Lu[BUCKET_MAX];
+    bool has_dec = false;
+#pragma unroll
+    for (int q = 0; q < BUCKET_MAX; q++) {
+        const uint32_t u = var[q];
+        const bool in = (uint32_t)q < L;
+        has_dec |= in && u != x && u == X.dec_v;
+        Lu[q] = (in && u != x && u != X.dec_v) ? __ldcg(D.dl + u) : 0;
+    }
+    for (uint32_t w = lane; w < nw; w += 32u) {
+        unsigned long long acc = (has_dec && w == (dbit >> 6)) ? (1ull << (dbit & 63u)) : 0ull;
+#pragma unroll
+        for (int q = 0; q < BUCKET_MAX; q++)
+            if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= __ldcg(D.deps + (size_t)var[q] * D.WW + w);
+        D.deps[(size_t)x * D.WW + w] = acc;
+    }
+}
+
 // U groups of 32 nogoods of bucket L, lane = nogood k0 + t*stride + lane.
 // All literals are loaded (coalesced, one row per literal position) and
 // their values gathered before any is classified: a nogood is satisfied if
@@ -743,9 +770,88 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
     }
 }
 
+// Frontier round: only the bucket nogoods that contain a variable of the
+// trail entries [fr0, fr1) (the previous round's assignments), or this
+// phase's decision variable X.dec_v when there is one, can have become unit
+// or violated since the last round; every other bucket nogood is as the
+// last sweep left it.  One warp per variable (round-robin over CTAs first),
+// one lane per nogood of its occurrence list, classified against the global
+// codes (this round's claims read as unassigned; the decision variable,
+// whose code the leader may still be writing, as true).
+__device__ __forceinline__ void frontier_round(const SweepCtx &X, uint32_t fr0, uint32_t fr1, unsigned long long &checks)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t wpc = blockDim.x >> 5, slot = (X.gw % wpc) * (X.nw / wpc) + X.gw / wpc;
+    const bool dec = X.dec_v != 0xFFFFFFFFu;
+    const uint32_t count = dec ? 1u : fr1 - fr0;
+    for (uint32_t i = slot; i < count; i += X.nw) {
+        const uint32_t v = dec ? X.dec_v : __ldcg(D.trail + fr0 + i) & TRAIL_VAR;
+        if (v >= D.nv) continue;
+        const uint32_t o0 = __ldg(D.occ_off + v), o1 = __ldg(D.occ_off + v + 1u);
+        for (uint32_t ob = o0; ob < o1; ob += 32u) {
+            const uint32_t o = ob + lane;
+            const bool has = o < o1;
+            const uint32_t id = has ? __ldg(D.occ + o) : 0u;
+            const uint32_t L = has ? ((id >> 27) & 15u) + 1u : 0u, k = id & 0x7FFFFFFu;
+            const uint32_t *base = has ? D.lits + D.bk_base[L] + k : D.lits;
+            const uint32_t n = has ? D.bk_n[L] : 0u;
+            uint32_t lit[BUCKET_MAX];
+#pragma unroll
+            for (int q = 0; q < BUCKET_MAX; q++) lit[q] = (uint32_t)q < L ? __ldg(base + (size_t)q * n) : 0u;
+            bool sat = false;
+            uint32_t n_un = 0, ul = 0;
+#pragma unroll
+            for (int q = 0; q < BUCKET_MAX; q++) {
+                if ((uint32_t)q >= L) continue;
+                const uint32_t u = lit[q] >> 1;
+                const uint32_t val = u == X.dec_v ? V_T : global_val(D, u, X.fresh);
+                sat |= val == ((lit[q] & 1u) ? V_T : V_F);
+                if (val == 0u) { n_un++; ul = lit[q]; }
+            }
+            checks += L;
+            bool won = false;
+            uint32_t x = 0, valbit = 0;
+            if (has && !sat && n_un == 0u) {
+                report_conflict(X, id, L);
+            } else if (has && !sat && n_un == 1u) {
+                if (!X.do_claim) {
+                    atomicAdd(&X.acc->flag, 1u);
+                } else {
+                    x = ul >> 1;
+                    valbit = (ul & 1u) ? V_T : V_F;
+                    const int r = claim_var(D.asg, x, valbit, X.fresh);
+                    if (r == 2) report_conflict(X, id, L);
+                    else if (r == 0) { record_claim(X, x, valbit, id); won = true; }
+                }
+            }
+            if (X.cdl > 1u) {
+                unsigned m = __ballot_sync(FULL_MASK, won);
+                if (m) {
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1u;
+                        uint32_t var[BUCKET_MAX];
+#pragma unroll
+                        for (int q = 0; q < BUCKET_MAX; q++) var[q] = __shfl_sync(FULL_MASK, lit[q], src) >> 1;
+                        warp_deps_dyn(X, var, __shfl_sync(FULL_MASK, L, src), __shfl_sync(FULL_MASK, x, src));
+                    }
+                    __threadfence_block();
+                    __syncwarp();
+                }
+            }
+            if (won && X.use_view) {
+                __threadfence_block();
+                view_set(X.V, x, valbit);
+            }
+        }
+    }
+}
+
 // Propagate-and-check over this CTA's ranges of every bucket, then
 // (grid-wide) the static long nogoods and the learned nogoods.
-__device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned)
+__device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bool full = true,
+                                      uint32_t fr0 = 0u, uint32_t fr1 = 0u)
 {
     SweepCtx X = X0;
     X.listed = X0.do_claim;
@@ -770,7 +876,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned)
         const uint32_t groups = (n + 31u) >> 5, per = unit_groups(L);
         ubase[L + 1] = ubase[L] + (groups + per - 1u) / per;
     }
-    const uint32_t units = ubase[BUCKET_MAX + 1];
+    const uint32_t units = full ? ubase[BUCKET_MAX + 1] : 0u;
     // Long and learned nogoods first (one warp each, round-robin over CTAs
     // first, then over the warps of a CTA); the warps that take one then
     // take fewer bucket units from the queue.
@@ -797,6 +903,11 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned)
         if (D.view_mode == VIEW_BYTES) run_unit_view<true>(X, L, k0, b1);
         else if (D.view_mode == VIEW_PACKED) run_unit_view<false>(X, L, k0, b1);
         else run_unit(X, L, k0, b1);
+    }
+    if (!full) {
+        unsigned long long fchecks = 0;           // per lane (classify_long's are per warp)
+        frontier_round(X, fr0, fr1, fchecks);
+        checks += __reduce_add_sync(FULL_MASK, (unsigned)fchecks);
     }
     if (lane == 0 && checks) atomicAdd(&X.acc->checks, checks);
     if (timer) {
@@ -1163,8 +1274,8 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
 
         // the propagate-and-check sweep of ROUND and APPLY runs after the
         // switch (one copy of its code)
-        bool sw = false;
-        uint32_t sw_cdl = 0, sw_tbase = 0, sw_dec = 0xFFFFFFFFu;
+        bool sw = false, sw_full = true;
+        uint32_t sw_cdl = 0, sw_tbase = 0, sw_dec = 0xFFFFFFFFu, sw_fr0 = 0, sw_fr1 = 0;
         switch (C.op) {
         case OP_INIT: {
             SweepCtx X{&D, V, fresh_cur, 1u, tend, acc, true, false, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
@@ -1184,7 +1295,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 }
             }
             if (leader) {
-                N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = C.tc; N.clean = 0;
+                N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = C.tc; N.clean = 0; N.full = 1;
             }
             break;
         }
@@ -1262,11 +1373,13 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             cta_sync();
             sw = true; sw_cdl = C.cdl; sw_tbase = tend;
+            sw_full = C.full != 0u || !D.frontier;
+            sw_fr0 = C.tc; sw_fr1 = tend;
             if (leader) {
-                N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1;
+                N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1; N.full = 0;
                 atomicAdd(&D.stats->rounds, 1ull);
                 atomicAdd(&D.stats->props, (unsigned long long)(tend - C.tc));
-                atomicAdd(&D.stats->checks, D.static_checks);
+                if (sw_full) atomicAdd(&D.stats->checks, D.static_checks);
             }
             break;
         }
@@ -1287,7 +1400,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     }
                 }
                 if (leader) {
-                    N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = tend; N.clean = 0;
+                    N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = tend; N.clean = 0; N.full = 0;
                     atomicAdd(&D.stats->completions, 1ull);
                 }
                 break;
@@ -1310,12 +1423,13 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             if (threadIdx.x == 0) view_set(V, bv, V_T);
             cta_sync();
             sw = true; sw_cdl = L; sw_tbase = tend + 1u; sw_dec = bv;
+            sw_full = !D.frontier;
             if (leader) {
                 N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
-                N.clean = 0;
+                N.clean = 0; N.full = 0;
                 atomicAdd(&D.stats->decisions, 1ull);
                 atomicAdd(&D.stats->rounds, 1ull);
-                atomicAdd(&D.stats->checks, D.static_checks);
+                if (sw_full) atomicAdd(&D.stats->checks, D.static_checks);
                 if ((unsigned long long)L > D.stats->max_level) D.stats->max_level = L;
             }
             break;
@@ -1332,7 +1446,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             for (uint32_t i = newend + threadIdx.x; i < tend; i += blockDim.x)
                 view_clear(V, __ldcg(D.trail + i) & TRAIL_VAR);
             if (leader) {
-                N.op = OP_ROUND; N.cdl = C.target; N.tc = newend; N.tb = newend; N.clean = 0;
+                N.op = OP_ROUND; N.cdl = C.target; N.tc = newend; N.tb = newend; N.clean = 0; N.full = 1;
             }
             break;
         }
@@ -1499,7 +1613,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         if (sw) {
             const unsigned long long ts = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
             SweepCtx X{&D, V, fresh_cur, sw_cdl, sw_tbase, acc, true, true, sw_dec, cta, rank >> 5, size >> 5};
-            sweep(X, C.n_learned);
+            sweep(X, C.n_learned, sw_full, sw_fr0, sw_fr1);
             if (threadIdx.x == 0) atomicMax(&acc->tsweep, globaltimer_ns() - ts);
         }
 

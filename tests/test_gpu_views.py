@@ -131,3 +131,74 @@ def test_batch_in_every_view(gpu, mode):
         assert st[i] == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT), i
         for m in models[i]:
             assert oracle.is_answer_set(p, m)
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("grid", [1, 0])
+@pytest.mark.parametrize("seed", range(5))
+def test_frontier_propagation_reaches_the_same_fixpoint(gpu, mode, grid, seed):
+    """Rounds that check only the nogoods of the last round's assignments
+    (full sweeps after (re)starts) reach the unique UP closure."""
+    prog = random_program(300 + 53 * seed, 900 + 151 * seed, program_seed(608, seed))
+    P = gpu.Program(prog, view_mode=mode, grid_ctas=grid, frontier=True)
+    perm = _gpu_to_oracle_perm(prog)
+    rng = np.random.default_rng(3000 + seed)
+    for _ in range(3):
+        partial = np.zeros(P.n_vars, np.int8)
+        k = int(rng.integers(1, 25))
+        pick = rng.choice(prog.n_atoms, size=k, replace=False)
+        partial[pick] = rng.choice([-1, 1], size=k)
+        conflict, clo = P.propagate(partial)
+        opart = np.zeros(P.n_vars, np.int8)
+        opart[perm] = partial
+        oconf, oclo, _, _ = oracle.up_closure(prog, opart)
+        assert conflict == oconf
+        if not oconf:
+            assert (clo == oclo[perm]).all()
+
+
+@pytest.mark.parametrize("index", [3, 77, 151, 402, 555, 918])
+def test_frontier_tiny_full_enumeration(gpu, index):
+    prog = tiny_program(index)
+    want = _sets(oracle.brute_force(prog))
+    status, models, n = gpu.Program(prog, frontier=True).solve(0, cap=1 << 12)
+    assert _sets(models) == want and n == len(want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_frontier_search_answers_and_bitmaps(gpu, seed):
+    prog = random_program(700, 1400, program_seed(609, seed))
+    ost, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=30)
+    assert ost in (oracle.SAT, oracle.UNSAT)
+    P = gpu.Program(prog, frontier=True, time_budget_ms=30_000)
+    st, models, _ = P.solve(1, cap=1)
+    assert st == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT)
+    for m in models:
+        assert oracle.is_answer_set(prog, m)
+    s = P.state(deps_words=64)
+    lvl, rea, deps = s["level"], s["reason"], s["deps"]
+    W = deps.shape[1]
+    for v in s["trail"]:
+        L = int(lvl[v])
+        if L <= 1 or rea[v] in (gpu.R_DECISION, gpu.R_COMPLETE):
+            continue
+        nw = min(W, (L + 63) // 64)
+        want = np.zeros(nw, np.uint64)
+        for lit in P.nogood(int(rea[v])):
+            u = lit >> 1
+            if u == v or lvl[u] <= 1:
+                continue
+            want |= deps[u, :nw] & _mask(min(W, (int(lvl[u]) + 63) // 64), nw)
+        assert (deps[v, :nw] == want).all(), v
+
+
+def test_frontier_batch(gpu):
+    progs = batch_programs(10, rules_per_atom=2, lo=50, hi=1500, config_id=610)
+    P = [gpu.Program(p, frontier=True, time_budget_ms=20_000) for p in progs]
+    st, nm, models = gpu.solve_batch(P, max_models_each=1, cap_each=1)
+    for i, p in enumerate(progs):
+        ost, _, _ = oracle.cdnl(p, max_models=1, time_budget_s=30)
+        assert ost in (oracle.SAT, oracle.UNSAT)
+        assert st[i] == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT), i
+        for m in models[i]:
+            assert oracle.is_answer_set(p, m)
