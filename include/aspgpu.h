@@ -175,7 +175,7 @@ typedef struct asp_batch asp_batch;
  * 0 = 256 threads per CTA, 3 CTAs per SM; 1 = 128 threads, 6 per SM (twice
  * the programs in flight, smaller shared-memory views).  config =
  * ASP_BATCH_AUTOTUNE runs each configuration once on a sample of up to 256
- * programs spread over the queue (each with at most 32 conflicts and 2 s of
+ * programs spread over the queue (each with at most 8 conflicts and 0.5 s of
  * device time) and keeps the one with the lower device time per program (the trial solves change nothing but the programs' last
  * results).  models_cap may be NULL (no models kept).  The programs must
  * stay loaded until asp_batch_free.  Errors: ASP_E_ARG, ASP_E_OOM,

@@ -301,7 +301,7 @@ namespace {
 // autotuner trials solve each sampled program with at most this many
 // conflicts and this much device time (the same short work for every
 // configuration)
-constexpr long long TRIAL_CONFLICTS = 32, TRIAL_TIME_NS = 2000000000ll;
+constexpr long long TRIAL_CONFLICTS = 8, TRIAL_TIME_NS = 500000000ll;
 
 // descriptors of every program of the batch for kernel configuration
 // `config` (trial: the autotuner's shortened budgets)
@@ -937,7 +937,7 @@ int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each,
     int chosen = config < 0 ? 0 : config;
     if (config == ASP_BATCH_AUTOTUNE) {
         // each configuration solves the same sample (up to 256 programs spread
-        // over the queue order, at most 32 conflicts and 2 s each) once; the
+        // over the queue order, at most 8 conflicts and 0.5 s each) once; the
         // lower device time per program wins
         const size_t S = std::min<size_t>((size_t)n, 256);
         std::vector<uint32_t> sample(S);
