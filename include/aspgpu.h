@@ -83,7 +83,8 @@ typedef struct {
                                  deeper levels share one overflow bit. 0 = 4096 */
     int64_t conflict_budget;  /* stop with UNKNOWN after this many conflicts; 0 = none */
     int64_t time_budget_ms;   /* stop with UNKNOWN after this device time; 0 = none */
-    int64_t learned_capacity; /* literals reserved for learned nogoods; 0 = automatic */
+    int64_t learned_capacity; /* literals reserved for learned nogoods; 0 = automatic
+                                 (8 x the static store, at least 2^24, at most 2^28) */
     int32_t grid_ctas;        /* CTAs of the persistent solver grid; 0 = one per SM */
     int32_t block_threads;    /* threads per CTA (multiple of 32, <= 768); 0 = 768 */
     void *cuda_stream;        /* cudaStream_t for all work of this program; NULL = default */

@@ -449,7 +449,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.lits_static = (uint32_t)lits.size();
     D.static_checks = bucket_lits;
     int64_t lcap = p->opt.learned_capacity > 0 ? p->opt.learned_capacity
-                                               : std::min<int64_t>(std::max<int64_t>(1 << 22, 4 * (int64_t)lits.size()), 1 << 28);
+                                               : std::min<int64_t>(std::max<int64_t>(1 << 24, 8 * (int64_t)lits.size()), 1 << 28);
     if ((int64_t)D.lits_static + lcap + 128 >= (int64_t)0xFFFFFF00ll) lcap = (int64_t)0xFFFFFF00ll - D.lits_static - 128;
     D.lits_cap = (uint32_t)(D.lits_static + lcap);
     D.learned_ng_cap = (uint32_t)std::min<int64_t>(lcap / 2 + 1024, 1 << 28);
