@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--conflicts", type=int, default=200, help="conflict budget per step")
     ap.add_argument("--view", type=int, default=0, help="sweep view layout: 0 auto, 1 plain, 2 packed, 3 bytes")
     ap.add_argument("--frontier", action="store_true", help="frontier rounds (full sweeps after backjumps)")
+    ap.add_argument("--save-weights", default="", help="write the trained heuristic weights to this JSON file")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample length")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -412,8 +413,8 @@ def _learned(a, aspgpu, torch):
     w, tstats = H.fit(X, y)
     ws, sstats = H.fit(X, y, static=True)
     t_train = time.perf_counter() - t0
-    H.save(w, os.path.join(ROOT, "gpurun_out", "heuristic_mlp.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-           else os.devnull, **tstats)
+    if a.save_weights:
+        H.save(w, a.save_weights, **tstats)
     evalp = _a11_programs(a.learned, 2 * 10**6)
     out = {}
     for name, kw in (("plain", dict(heuristic=0)), ("learned", dict(heuristic=2, mlp_weights=w)),
