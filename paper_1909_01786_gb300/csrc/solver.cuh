@@ -438,17 +438,10 @@ __device__ __forceinline__ void warp_deps(const SweepCtx &X, const uint32_t (&va
         Lu[q] = (u != x && u != X.dec_v) ? __ldcg(D.dl + u) : 0;
     }
     for (uint32_t w = lane; w < nw; w += 32u) {
-        // the bitmap words are loaded together with the levels above (words
-        // past a variable's level, or of variables at level <= 1, are read
-        // and dropped), so a claim waits for one round trip, not two
-        unsigned long long word[L];
-#pragma unroll
-        for (int q = 0; q < L; q++)
-            word[q] = (var[q] != x && var[q] != X.dec_v) ? __ldcg(D.deps + (size_t)var[q] * D.WW + w) : 0ull;
         unsigned long long acc = (has_dec && w == (dbit >> 6)) ? (1ull << (dbit & 63u)) : 0ull;
 #pragma unroll
         for (int q = 0; q < L; q++)
-            if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= word[q];
+            if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= __ldcg(D.deps + (size_t)var[q] * D.WW + w);
         D.deps[(size_t)x * D.WW + w] = acc;
     }
 }
