@@ -493,7 +493,7 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
 #pragma unroll
         for (int q = 0; q < L; q++) lit[t][q] = k < k1 ? __ldg(base + (size_t)q * n + k) : PAD_LIT;
     }
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < 2; pass++) {
         uint32_t val[U][L];
 #pragma unroll
         for (int t = 0; t < U; t++)
@@ -572,7 +572,7 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
 #pragma unroll
         for (int q = 0; q < L; q++) lit[t][q] = __ldg(base + (size_t)q * n + k);
     }
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < 2; pass++) {
         uint32_t cnt[U];
 #pragma unroll
         for (int t = 0; t < U; t++) {
