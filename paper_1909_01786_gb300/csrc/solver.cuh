@@ -329,6 +329,9 @@ struct SweepCtx {
 };
 
 constexpr uint32_t CLAIM_BUF = 256;
+// first unit of each bucket in this CTA's part of the partition (units of
+// unit_groups(L) groups of 32 nogoods); entry BUCKET_MAX + 1 = all units
+__shared__ uint32_t s_ubase[BUCKET_MAX + 2];
 __shared__ uint32_t s_claims[CLAIM_BUF];
 __shared__ unsigned int s_ncl, s_cbase;
 // CTA 0, thread 0: time in the sweeps on long and learned nogoods and on
@@ -848,6 +851,22 @@ __device__ __forceinline__ void frontier_round(const SweepCtx &X, uint32_t fr0, 
     }
 }
 
+// The CTA's unit table (s_ubase) from the static partition, once per
+// launch; callers synchronise the CTA before the first sweep.
+__device__ __forceinline__ void unit_table(const Dev &D, uint32_t cta)
+{
+    if (threadIdx.x != 0) return;
+    const uint32_t G1 = D.G + 1u;
+    uint32_t acc = 0;
+    for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
+        s_ubase[L] = acc;
+        const uint32_t n = __ldg(D.cta_boff + L * G1 + cta + 1u) - __ldg(D.cta_boff + L * G1 + cta);
+        const uint32_t groups = (n + 31u) >> 5, per = unit_groups(L);
+        acc += (groups + per - 1u) / per;
+    }
+    s_ubase[BUCKET_MAX + 1] = acc;
+}
+
 // Propagate-and-check over this CTA's ranges of every bucket, then
 // (grid-wide) the static long nogoods and the learned nogoods.
 __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bool full = true,
@@ -868,14 +887,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     cta_sync();                       // the previous sweep's warps are done with it
     if (threadIdx.x == 0) { s_unit = 0u; s_ncl = 0u; }
     cta_sync();
-    uint32_t ubase[BUCKET_MAX + 2];
-    ubase[2] = 0u;
-#pragma unroll
-    for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
-        const uint32_t n = __ldg(D.cta_boff + L * G1 + X.cta + 1u) - __ldg(D.cta_boff + L * G1 + X.cta);
-        const uint32_t groups = (n + 31u) >> 5, per = unit_groups(L);
-        ubase[L + 1] = ubase[L] + (groups + per - 1u) / per;
-    }
+    const uint32_t *const ubase = s_ubase;     // set up once per launch (unit_table)
     const uint32_t units = full ? ubase[BUCKET_MAX + 1] : 0u;
     // Long and learned nogoods first (one warp each, round-robin over CTAs
     // first, then over the warps of a CTA); the warps that take one then
@@ -893,10 +905,11 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         if (lane == 0) u = atomicAdd(&s_unit, 1u);
         u = __shfl_sync(FULL_MASK, u, 0);
         if (u >= units) break;
-        uint32_t L = 2, first = 0;
+        uint32_t L = 2;
 #pragma unroll
         for (uint32_t q = 3; q <= (uint32_t)BUCKET_MAX; q++)
-            if (u >= ubase[q]) { L = q; first = ubase[q]; }
+            if (u >= ubase[q]) L = q;
+        const uint32_t first = ubase[L];
         const uint32_t b0 = __ldg(D.cta_boff + L * G1 + X.cta);
         const uint32_t b1 = __ldg(D.cta_boff + L * G1 + X.cta + 1u);
         const uint32_t k0 = b0 + (u - first) * unit_groups(L) * 32u;
@@ -1249,6 +1262,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     }
     cta_sync();
     view_reload(D, V, 4u << (sC.round & 1u));
+    unit_table(D, cta);
     cta_sync();
 
     for (uint32_t k = 0;; k++) {

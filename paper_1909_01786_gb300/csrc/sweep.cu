@@ -13,6 +13,7 @@ __global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc, uint32_t
     uint32_t *vbase = reinterpret_cast<uint32_t *>(smem_raw + D.WW + 32) + 16;
     const View V = make_view(D, vbase, blockIdx.x);
     view_reload(D, V, 0u);
+    unit_table(D, blockIdx.x);
     cta_sync();
     for (uint32_t pass = 1; pass < passes; pass++) {
         SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
