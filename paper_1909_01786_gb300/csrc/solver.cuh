@@ -332,6 +332,8 @@ constexpr uint32_t CLAIM_BUF = 256;
 // first unit of each bucket in this CTA's part of the partition (units of
 // unit_groups(L) groups of 32 nogoods); entry BUCKET_MAX + 1 = all units
 __shared__ uint32_t s_ubase[BUCKET_MAX + 2];
+// this CTA's range [s_krange[L][0], s_krange[L][1]) of bucket L
+__shared__ uint32_t s_krange[BUCKET_MAX + 1][2];
 __shared__ uint32_t s_claims[CLAIM_BUF];
 __shared__ unsigned int s_ncl, s_cbase;
 // CTA 0, thread 0: time in the sweeps on long and learned nogoods and on
@@ -860,7 +862,9 @@ __device__ __forceinline__ void unit_table(const Dev &D, uint32_t cta)
     uint32_t acc = 0;
     for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
         s_ubase[L] = acc;
-        const uint32_t n = __ldg(D.cta_boff + L * G1 + cta + 1u) - __ldg(D.cta_boff + L * G1 + cta);
+        s_krange[L][0] = __ldg(D.cta_boff + L * G1 + cta);
+        s_krange[L][1] = __ldg(D.cta_boff + L * G1 + cta + 1u);
+        const uint32_t n = s_krange[L][1] - s_krange[L][0];
         const uint32_t groups = (n + 31u) >> 5, per = unit_groups(L);
         acc += (groups + per - 1u) / per;
     }
@@ -876,7 +880,6 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     X.listed = X0.do_claim;
     const Dev &D = *X.D;
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t G1 = D.G + 1u;
     const bool timer = X.cta == 0 && threadIdx.x == 0 && X.do_claim;
     const unsigned long long t0 = timer ? globaltimer_ns() : 0ull;
     // Units of work (one bucket, unit_groups(L) consecutive groups of 32
@@ -910,8 +913,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         for (uint32_t q = 3; q <= (uint32_t)BUCKET_MAX; q++)
             if (u >= ubase[q]) L = q;
         const uint32_t first = ubase[L];
-        const uint32_t b0 = __ldg(D.cta_boff + L * G1 + X.cta);
-        const uint32_t b1 = __ldg(D.cta_boff + L * G1 + X.cta + 1u);
+        const uint32_t b0 = s_krange[L][0], b1 = s_krange[L][1];
         const uint32_t k0 = b0 + (u - first) * unit_groups(L) * 32u;
         if (D.view_mode == VIEW_BYTES) run_unit_view<true>(X, L, k0, b1);
         else if (D.view_mode == VIEW_PACKED) run_unit_view<false>(X, L, k0, b1);
