@@ -336,6 +336,9 @@ __shared__ uint32_t s_ubase[BUCKET_MAX + 2];
 __shared__ uint32_t s_krange[BUCKET_MAX + 1][2];
 __shared__ uint32_t s_claims[CLAIM_BUF];
 __shared__ unsigned int s_ncl, s_cbase;
+// next bucket unit of the CTA's queue in the current sweep (solver sweeps;
+// sweeps that do not claim alternate between s_unit2[0] and s_unit2[1])
+__shared__ unsigned int s_unit, s_unit2[2];
 // CTA 0, thread 0: time in the sweeps on long and learned nogoods and on
 // the buckets
 __shared__ unsigned long long s_tlearned, s_tbuckets;
@@ -858,6 +861,10 @@ __device__ __forceinline__ void frontier_round(const SweepCtx &X, uint32_t fr0, 
 __device__ __forceinline__ void unit_table(const Dev &D, uint32_t cta)
 {
     if (threadIdx.x != 0) return;
+    s_unit = 0u;
+    s_ncl = 0u;
+    s_unit2[0] = 0u;
+    s_unit2[1] = 0u;
     const uint32_t G1 = D.G + 1u;
     uint32_t acc = 0;
     for (uint32_t L = 2; L <= (uint32_t)BUCKET_MAX; L++) {
@@ -874,7 +881,7 @@ __device__ __forceinline__ void unit_table(const Dev &D, uint32_t cta)
 // Propagate-and-check over this CTA's ranges of every bucket, then
 // (grid-wide) the static long nogoods and the learned nogoods.
 __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bool full = true,
-                                      uint32_t fr0 = 0u, uint32_t fr1 = 0u)
+                                      uint32_t fr0 = 0u, uint32_t fr1 = 0u, uint32_t pass = 0u)
 {
     SweepCtx X = X0;
     X.listed = X0.do_claim;
@@ -886,10 +893,17 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     // nogoods) are taken from a per-CTA counter, bucket after bucket, so
     // every warp runs about the same number of load-gather-classify chains
     // whatever the mix of lengths.
-    __shared__ unsigned int s_unit;
-    cta_sync();                       // the previous sweep's warps are done with it
-    if (threadIdx.x == 0) { s_unit = 0u; s_ncl = 0u; }
-    cta_sync();
+    // The counters start at 0: reset at launch (unit_table) and, in the
+    // solver, at the end of every sweep once no warp reads them any more.
+    // Sweeps that do not claim (the sweep timed alone, `pass` = its index
+    // in the launch) use two counters: after one barrier no warp is in the
+    // previous sweep, so its counter can be cleared for the next one.
+    unsigned int *uctr = &s_unit;
+    if (!X.do_claim) {
+        cta_sync();
+        if (threadIdx.x == 0) s_unit2[(pass + 1u) & 1u] = 0u;
+        uctr = &s_unit2[pass & 1u];
+    }
     const uint32_t *const ubase = s_ubase;     // set up once per launch (unit_table)
     const uint32_t units = full ? ubase[BUCKET_MAX + 1] : 0u;
     // Long and learned nogoods first (one warp each, round-robin over CTAs
@@ -905,7 +919,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
     for (;;) {
         uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(&s_unit, 1u);
+        if (lane == 0) u = atomicAdd(uctr, 1u);
         u = __shfl_sync(FULL_MASK, u, 0);
         if (u >= units) break;
         uint32_t L = 2;
@@ -935,6 +949,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         // then every thread copies (no barrier under a data-dependent branch)
         cta_sync();
         const uint32_t n = min(s_ncl, CLAIM_BUF);
+        if (threadIdx.x == 0) s_unit = 0u;          // every warp has left the unit queue
         if (threadIdx.x < 32u) {
             uint32_t base = 0;
             if (threadIdx.x == 0 && n) base = atomicAdd(&X.acc->nclaim, n);
@@ -943,6 +958,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         }
         cta_sync();
         const uint32_t b = s_cbase;
+        if (threadIdx.x == 0) s_ncl = 0u;           // every thread has read n
         for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
             if (b + k < D.nv) D.trail[b + k] = s_claims[k];
     }

@@ -15,14 +15,11 @@ __global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc, uint32_t
     view_reload(D, V, 0u);
     unit_table(D, blockIdx.x);
     cta_sync();
-    for (uint32_t pass = 1; pass < passes; pass++) {
+    for (uint32_t pass = 0; pass < (passes ? passes : 1u); pass++) {
         SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
                    (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
-        sweep(X, 0u);
+        sweep(X, 0u, true, 0u, 0u, pass);
     }
-    SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
-               (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
-    sweep(X, 0u);
 }
 
 cudaError_t sweep_configure()
