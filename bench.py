@@ -190,6 +190,20 @@ def _program_small():
     return random_program(50, 100, program_seed(2, 1))
 
 
+def aggregate_over_ranks(ms, checks, world, device):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    and the checks of all ranks (one all-reduce each; nothing when N = 1)."""
+    if world <= 1:
+        return float(ms), float(checks)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(checks)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     from paper_1909_01786_gb300 import aspgpu
@@ -243,15 +257,7 @@ def run_ours(a, rank, world, local_rank):
         barrier()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     checks = totals["literal_checks"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        c = torch.tensor([float(checks)], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        ms, checks_all = float(t.item()), float(c.item())
-    else:
-        checks_all = float(checks)
+    ms, checks_all = aggregate_over_ranks(ms, checks, world, dev)
     value = checks_all / (ms / 1e3)
 
     # dominant kernel: the persistent solve kernel (one launch per step)
