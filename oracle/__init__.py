@@ -155,3 +155,37 @@ def cdnl(prog, max_models: int = 0, conflict_budget: int = 0, time_budget_s: flo
     stats = dict(decisions=int(st[0]), conflicts=int(st[1]), propagations=int(st[2]),
                  learned=int(st[3]), literal_checks=int(st[4]), n_models=int(nm.value))
     return status, buf[:n, :prog.n_atoms].copy(), stats
+
+
+def first_uip(delta, position, level, antecedent):
+    """Resolution-based conflict analysis to the first UIP (Section 4.2,
+    Algorithm 3), in plain Python over a given solver state.
+
+    delta         the violated nogood: literals (var, is_false), all holding
+    position[v]   trail position of assigned variable v (assignment order)
+    level[v]      decision level of v (1 = the root)
+    antecedent(v) the nogood that assigned v: literals (var, is_false) that
+                  hold, plus the complement of v's own literal; None for a
+                  decision
+
+    Loop of Algorithm 3: sigma = the literal of delta assigned last; kappa =
+    the highest level among the other literals of delta (0 if there are
+    none); if kappa = dl(sigma), delta becomes the resolvent
+    (delta minus sigma) united with (antecedent(sigma) minus the complement
+    of sigma); otherwise (delta, kappa) is the result.  Returns
+    (learned literals as a set, kappa, sigma = the first UIP).
+    """
+    d = set(delta)
+    while True:
+        sigma = max(d, key=lambda l: position[l[0]])
+        kappa = max([level[v] for (v, f) in d if (v, f) != sigma] + [0])
+        if kappa != level[sigma[0]]:
+            return d, kappa, sigma
+        eps = antecedent(sigma[0])
+        if eps is None:
+            raise ValueError("a decision shares its level with another literal of the nogood")
+        comp = (sigma[0], not sigma[1])
+        eps = set(eps)
+        if comp not in eps:
+            raise ValueError("the antecedent does not contain the complement of the literal")
+        d = (d - {sigma}) | (eps - {comp})
