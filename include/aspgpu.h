@@ -71,6 +71,19 @@ extern "C" {
 #define ASP_VIEW_PACKED 2
 #define ASP_VIEW_BYTES 3
 
+/* Conflict analysis (Section 4.2).  FWD: fwd-learning -- the learned
+ * nogood is the decision literals of the levels in the OR of the conflict's
+ * dependency bitmaps, and the search backjumps to the level below the
+ * highest of them.  RES: resolution to the first UIP (Algorithm 3, the
+ * analysis the paper compares fwd-learning against), run by one warp: the
+ * learned nogood holds the first UIP of the conflict level and the literals
+ * below it that the resolution reaches, and the search backjumps to the
+ * highest level among the latter.  Root-level literals are left out of
+ * either.  RES keeps a trail position, a stamp and a bit per variable (12
+ * bytes per variable more). */
+#define ASP_LEARN_FWD 0
+#define ASP_LEARN_RES 1
+
 #define ASP_MLP_FEATURES 16   /* inputs of the learned heuristic per candidate rule */
 #define ASP_MLP_PARAMS 1153   /* W1[64][16], b1[64], w2[64], b2 */
 
@@ -105,6 +118,8 @@ typedef struct {
        nogood-by-variable occurrence lists built at load), full sweeps after
        backjumps; 0: every round sweeps every nogood */
     int32_t frontier;
+    /* ASP_LEARN_*: conflict analysis */
+    int32_t learning;
 } asp_options;
 
 typedef struct {
@@ -231,6 +246,25 @@ int asp_sweep(asp_prog *p, int32_t passes);
  * buffers; any may be NULL.  *n_trail receives the trail length. */
 int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *level,
                     uint32_t *reason, uint64_t *deps, int32_t deps_words);
+
+/* The last conflict analysis of the last solve, for consistency checks.
+ * info (host int64[6]): {conflicting nogood id, trail length at the conflict
+ * (claims of the conflict round included), learned nogood id, its length,
+ * backjump target, level resolved at (ASP_LEARN_RES; 0 for ASP_LEARN_FWD)}.
+ * Length 0 and target 0: no conflict was analysed.  Length 0 and target
+ * t > 0: the resolution found the state inconsistent (the solve then ends
+ * with ASP_E_DEVICE) -- t numbers the failed check (1 literal outside the
+ * variables, 2 unassigned, 3 above the conflict level, 4 trail position
+ * outside its level, 5 nogood without end, 6/7 marked literals and count
+ * disagree, 8 trail entry outside the variables, 9 decision or input
+ * resolved upon, 10 empty level) and info[2] holds the variable or value
+ * involved.  trail (host, may be NULL) receives
+ * up to trail_cap entries of the trail at that point as literals
+ * (var << 1 | sign, sign 1 = F), in assignment order.  When the solve
+ * stopped on its conflict budget right after that analysis (before the
+ * backjump), levels and reasons from asp_debug_state describe the same
+ * assignment. */
+int asp_debug_last_conflict(asp_prog *p, int64_t *info, int32_t *trail, int64_t trail_cap);
 
 /* Literals of nogood `id` (a reason or learned id) as (var << 1 | sign),
  * sign 1 = F; returns the length, writes at most cap literals. */

@@ -20,6 +20,7 @@ MLP_FEATURES, MLP_PARAMS = 16, 1153
 HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED = 0, 1, 2
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 VIEW_AUTO, VIEW_PLAIN, VIEW_PACKED, VIEW_BYTES = 0, 1, 2, 3
+LEARN_FWD, LEARN_RES = 0, 1
 R_DECISION, R_COMPLETE, R_INPUT = 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD
 
 _lib = None
@@ -39,7 +40,7 @@ class Options(C.Structure):
                 ("block_threads", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
                 ("mlp_weights", C.c_void_p), ("trace_capacity", C.c_int64),
-                ("view_mode", C.c_int32), ("frontier", C.c_int32)]
+                ("view_mode", C.c_int32), ("frontier", C.c_int32), ("learning", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -54,7 +55,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
-           "asp_debug_state", "asp_debug_nogood", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
+           "asp_debug_state", "asp_debug_last_conflict", "asp_debug_nogood", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
            "asp_mlp_score", "asp_batch_create", "asp_batch_run", "asp_batch_info", "asp_batch_free"]
 
 
@@ -105,6 +106,8 @@ def lib(build_if_missing: bool = True):
         L.asp_sweep.restype = C.c_int
         L.asp_debug_state.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         L.asp_debug_state.restype = C.c_int
+        L.asp_debug_last_conflict.argtypes = [vp, vp, vp, i64]
+        L.asp_debug_last_conflict.restype = C.c_int
         L.asp_debug_nogood.argtypes = [vp, C.c_uint32, vp, i64]
         L.asp_debug_nogood.restype = i64
         L.asp_propagate_noalloc.argtypes = [vp, vp, vp, vp]
@@ -157,7 +160,7 @@ class Program:
 
     def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
                  learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True,
-                 mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False):
+                 mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False, learning=LEARN_FWD):
         L = lib()
         self.n_atoms = int(prog.n_atoms)
         self._keep = []
@@ -171,6 +174,7 @@ class Program:
         opt.trace_capacity = int(trace_capacity)
         opt.view_mode = int(view_mode)
         opt.frontier = 1 if frontier else 0
+        opt.learning = int(learning)
         opt.heuristic, opt.deps_levels = heuristic, deps_levels
         opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
         opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads
@@ -273,6 +277,24 @@ class Program:
                                      int(deps_words)))
         return dict(trail=trail[:nt.value], level=level[:nv], reason=reason[:nv],
                     deps=deps[:nv] if deps_words else None)
+
+    def last_conflict(self) -> dict | None:
+        """The last conflict analysis of the last solve (asp_debug_last_conflict):
+        conflicting nogood id, trail as literals up to the conflict, learned
+        nogood id and length, backjump target, level resolved at; None if no
+        conflict was analysed."""
+        info = np.zeros(6, np.int64)
+        trail = np.zeros(max(self.n_vars, 1), np.int32)
+        _check(lib().asp_debug_last_conflict(self.handle, info.ctypes.data, trail.ctypes.data, int(self.n_vars)))
+        nt = int(min(info[1], self.n_vars))
+        if info[3] == 0:
+            if info[4] == 0:
+                return None
+            # the analysis stopped on an inconsistent state
+            return dict(conflict=int(info[0]), trail=trail[:nt].copy(), failed_check=int(info[4]),
+                        involving=int(info[2]), level=int(info[5]))
+        return dict(conflict=int(info[0]), trail=trail[:nt].copy(), learned=int(info[2]),
+                    length=int(info[3]), target=int(info[4]), level=int(info[5]))
 
     def nogood(self, nid: int):
         buf = np.zeros(4096, np.int32)

@@ -461,6 +461,8 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.Wlevels = WW * 64u;
     D.heuristic = (uint32_t)std::max(0, p->opt.heuristic);
     if (D.heuristic > 3) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
+    if (p->opt.learning < 0 || p->opt.learning > 1) { delete p; return fail(ASP_E_ARG, "unknown learning"); }
+    D.learning = (uint32_t)p->opt.learning;
     p->n_nogoods = H.n_nogoods;
     p->n_literals = H.n_literals;
     p->n_units = (int64_t)H.units.size();
@@ -541,6 +543,17 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.bar = (Barrier *)alloc(sizeof(Barrier));
     p->d_result = (long long *)alloc(sizeof(long long) * 4);
     p->d_sweep_acc = (Acc *)alloc(sizeof(Acc));
+    if (D.learning) {
+        D.tpos = (uint32_t *)alloc((size_t)D.nv * 4 + 4);
+        D.stamp = (uint32_t *)alloc((size_t)D.nv * 4 + 4);
+        D.cand = (uint32_t *)alloc(((size_t)D.nv + 31) / 32 * 4 + 8);
+        D.epoch = (uint32_t *)alloc(16);
+        if (rc == ASP_OK) {
+            cudaError_t e = cudaMemsetAsync(D.stamp, 0, (size_t)D.nv * 4 + 4, p->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(D.epoch, 0, 16, p->stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "clear stamps");
+        }
+    }
     if (rc == ASP_OK && p->opt.frontier) {
         // per variable, the ids of the bucket nogoods it occurs in
         std::vector<uint32_t> off((size_t)D.nv + 1, 0), occ;
@@ -806,6 +819,32 @@ int asp_debug_state(asp_prog *p, int32_t *trail, int64_t *n_trail, int32_t *leve
                          cudaMemcpyDeviceToHost);
     }
     if (e != cudaSuccess) return cuda_fail(e, "state");
+    return ASP_OK;
+}
+
+int asp_debug_last_conflict(asp_prog *p, int64_t *info, int32_t *trail, int64_t trail_cap)
+{
+    if (!p || !info) return fail(ASP_E_ARG, "bad argument");
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    DevStats s;
+    e = cudaMemcpy(&s, p->D.stats, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "state");
+    info[0] = (int64_t)s.dbg_conf;
+    info[1] = (int64_t)s.dbg_tend;
+    info[2] = (int64_t)s.dbg_lfill;
+    info[3] = (int64_t)s.dbg_len;
+    info[4] = (int64_t)s.dbg_target;
+    info[5] = (int64_t)s.dbg_level;
+    const int64_t nt = std::min<int64_t>(std::min<int64_t>((int64_t)s.dbg_tend, (int64_t)p->D.nv), trail_cap);
+    if (trail && nt > 0) {
+        e = cudaMemcpy(trail, p->D.trail, (size_t)nt * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "state");
+        for (int64_t i = 0; i < nt; i++) {
+            const uint32_t t = (uint32_t)trail[i];
+            trail[i] = (int32_t)mk_lit(t & TRAIL_VAR, (t & TRAIL_F) != 0u);
+        }
+    }
     return ASP_OK;
 }
 

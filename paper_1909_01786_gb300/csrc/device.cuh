@@ -90,6 +90,10 @@ struct DevStats {
     // sums over phases of the slowest CTA's busy time and sweep time
     unsigned long long ns_slowest, ns_slowest_sweep;
     unsigned int trace_n, pad4;    // trace records written (atomic)
+    // the last conflict analysis: conflicting nogood, trail length (claims of
+    // the conflict round included), learned nogood id and length, backjump
+    // target, and the level the nogood was resolved at (0 for fwd-learning)
+    unsigned long long dbg_conf, dbg_tend, dbg_lfill, dbg_len, dbg_target, dbg_level;
 };
 
 // Grid barrier: arrivals counted since the solve began (barrier g is
@@ -143,6 +147,14 @@ struct Dev {
     uint32_t *reason;
     unsigned long long *deps;
     uint32_t *trail, *level_start, *dec_var, *lm;
+    // learning = 1 (Algorithm 3, resolution to the first UIP): trail
+    // position of each assigned variable (written with its trail entry), a
+    // per-variable stamp marking the variables of the nogood being resolved,
+    // a bitset over trail positions of its literals at the conflict level,
+    // and the stamp counter (one word, never reset: stamps of earlier
+    // analyses, in this solve or an earlier one, are all smaller)
+    uint32_t learning;
+    uint32_t *tpos, *stamp, *cand, *epoch;
     Ctl *ctl;
     Acc *acc;
     DevStats *stats;

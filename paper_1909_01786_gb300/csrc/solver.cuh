@@ -360,7 +360,10 @@ __device__ __forceinline__ void record_claim(const SweepCtx &X, uint32_t v, uint
         if (i < CLAIM_BUF) { s_claims[i] = entry; return; }
     }
     uint32_t pos = X.tbase + atomicAdd(&X.acc->nclaim, 1u);
-    if (pos < D.nv) D.trail[pos] = entry;
+    if (pos < D.nv) {
+        D.trail[pos] = entry;
+        if (D.tpos) D.tpos[v] = pos;
+    }
 }
 
 // One lane per literal u of a reason (has = false on lanes holding none):
@@ -884,7 +887,13 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
                                       uint32_t fr0 = 0u, uint32_t fr1 = 0u, uint32_t pass = 0u)
 {
     SweepCtx X = X0;
-    X.listed = X0.do_claim;
+    // Listed claims take their trail slots at the end of the sweep, after
+    // any claim that overflowed the list; a claim can rest on an earlier
+    // claim of its own CTA (published in the view), so listing breaks the
+    // trail's dependency order once the list overflows.  Resolution
+    // learning walks the trail backwards and needs that order: there every
+    // claim takes its slot when it is made.
+    X.listed = X0.do_claim && !X0.D->learning;
     const Dev &D = *X.D;
     const uint32_t lane = threadIdx.x & 31u;
     const bool timer = X.cta == 0 && threadIdx.x == 0 && X.do_claim;
@@ -960,7 +969,11 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         const uint32_t b = s_cbase;
         if (threadIdx.x == 0) s_ncl = 0u;           // every thread has read n
         for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
-            if (b + k < D.nv) D.trail[b + k] = s_claims[k];
+            if (b + k < D.nv) {
+                const uint32_t e = s_claims[k];
+                D.trail[b + k] = e;
+                if (D.tpos) D.tpos[e & TRAIL_VAR] = b + k;
+            }
     }
 }
 
@@ -1206,6 +1219,251 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
     cta_sync();
 }
 
+// Record of the last conflict analysis, for consistency checks (leader).
+__device__ __forceinline__ void debug_analysis(const Dev &D, uint32_t g, uint32_t tend, uint32_t lfill, uint32_t n,
+                                               uint32_t target, uint32_t m)
+{
+    D.stats->dbg_conf = g;
+    D.stats->dbg_tend = tend;
+    D.stats->dbg_lfill = lfill;
+    D.stats->dbg_len = n;
+    D.stats->dbg_target = target;
+    D.stats->dbg_level = m;
+}
+
+// ------------------------------------------------------ res-learning
+
+// State of the resolution chain of res_analyze (uniform over its warp).
+struct ResState {
+    uint32_t m;             // level the nogood is resolved at
+    uint32_t seg0, seg1;    // trail positions of level m
+    uint32_t ep;            // stamp of this analysis
+    uint32_t out0, nout;    // learned literals below level m: slots out0 ..
+    uint32_t kappa;         // highest level among them (1 if none)
+    bool err;
+    uint32_t why, what;     // failed check (1..10) and the variable or value involved
+};
+
+__device__ __forceinline__ void res_fail(ResState &R, uint32_t why, uint32_t what)
+{
+    if (!R.err) { R.why = why; R.what = what; }
+    R.err = true;
+}
+
+// The warp adds one literal per lane (has = false on lanes holding none) to
+// the nogood being resolved.  Dropped: the variable `skip` (the one resolved
+// upon), root-level literals and variables already in the nogood (stamped
+// with R.ep).  A literal at level m is marked in the trail-position bitset;
+// one below goes to the learned nogood.  Returns the number marked.
+__device__ __forceinline__ uint32_t res_add(const Dev &D, ResState &R, bool has, uint32_t l, uint32_t skip)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    bool cur = false, out = false;
+    uint32_t L = 0, bad = 0u;
+    if (has) {
+        const uint32_t u = l >> 1;
+        if (u >= D.nv) {
+            bad = 1u;
+        } else if (u != skip) {
+            const int32_t Ls = __ldcg(D.dl + u);
+            L = Ls > 0 ? (uint32_t)Ls : 0u;
+            if (L == 0u) {
+                bad = 2u;                // unassigned
+            } else if (L > R.m) {
+                bad = 3u;                // above the conflict level
+            } else if (L > 1u && atomicExch(D.stamp + u, R.ep) != R.ep) {
+                if (L == R.m) {
+                    const uint32_t tp = __ldcg(D.tpos + u);
+                    if (tp >= R.seg0 && tp < R.seg1) {
+                        atomicOr(D.cand + (tp >> 5), 1u << (tp & 31u));
+                        cur = true;
+                    } else {
+                        bad = 4u;        // trail position outside level m
+                    }
+                } else {
+                    out = true;
+                }
+            }
+        }
+    }
+    const unsigned bb = __ballot_sync(FULL_MASK, bad != 0u);
+    if (bb) {
+        const int src = __ffs(bb) - 1;
+        res_fail(R, __shfl_sync(FULL_MASK, bad, src), __shfl_sync(FULL_MASK, l >> 1, src));
+    }
+    const unsigned bc = __ballot_sync(FULL_MASK, cur), bo = __ballot_sync(FULL_MASK, out);
+    if (out) {
+        const uint32_t pos = R.out0 + R.nout + (uint32_t)__popc(bo & ((1u << lane) - 1u));
+        if (pos + 1u < D.lits_cap) D.lits[pos] = l;
+    }
+    R.nout += (uint32_t)__popc(bo);
+    uint32_t k = out ? L : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(FULL_MASK, k, o));
+    R.kappa = max(R.kappa, k);
+    return (uint32_t)__popc(bc);
+}
+
+// The literals of nogood `id` but variable `skip`, 32 at a time.
+__device__ __forceinline__ uint32_t res_add_nogood(const Dev &D, ResState &R, uint32_t id, uint32_t skip)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    if (id & BUCKET_ID) {
+        const uint32_t len = ng_len(D, id);               // at most BUCKET_MAX < 32
+        const bool has = lane < len;
+        return res_add(D, R, has, has ? ng_lit(D, id, lane) : 0u, skip);
+    }
+    uint32_t added = 0;
+    for (uint32_t base = 0;; base += 32u) {
+        if (id + base + 32u > D.lits_cap + 96u) { res_fail(R, 5u, id); break; }   // no end marker
+        const uint32_t w = lit_at(D, id + base + lane);
+        const unsigned Bend = __ballot_sync(FULL_MASK, (w & END_BIT) != 0u);
+        const unsigned valid = Bend ? ((2u << (__ffs(Bend) - 1)) - 1u) : FULL_MASK;
+        added += res_add(D, R, (valid >> lane) & 1u, w & ~END_BIT, skip);
+        if (Bend) break;
+    }
+    return added;
+}
+
+// The antecedent of a literal set by CompleteAssignment at level Le: the
+// decisions of levels 2 .. Le (each true).
+__device__ __forceinline__ uint32_t res_add_decisions(const Dev &D, ResState &R, uint32_t Le, uint32_t skip)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t added = 0;
+    for (uint32_t base = 2; base <= Le; base += 32u) {
+        const uint32_t lv = base + lane;
+        const bool has = lv <= Le;
+        added += res_add(D, R, has, has ? mk_lit(__ldcg(D.dec_var + lv), false) : 0u, skip);
+    }
+    return added;
+}
+
+// Conflict analysis by resolution to the first UIP (Algorithm 3), by one
+// warp of the analysing CTA.  delta starts as nogood g (every literal of it
+// holds; a variable both values were claimed for in the conflict round is
+// taken with its first claim) and m is its highest level.  Then, repeatedly:
+// sigma = the literal of delta at level m assigned last (highest trail
+// position); if no other literal of delta is at level m, sigma is the first
+// UIP and delta is learned with kappa = the highest level of the others;
+// else delta becomes the resolvent of delta and the reason of sigma (which
+// holds the complement of sigma).  Root-level literals are left out of
+// delta.  A literal set by CompleteAssignment has no reason nogood: its
+// antecedent is taken to be every decision up to its level.  Writes the
+// learned nogood at lfill, the first UIP first; S.misc: [0] = 1 conflict at
+// the root, 2 internal inconsistency, else 0; [1] = kappa (the backjump
+// target); [2] = length; [3] = m.
+__device__ __forceinline__ void res_analyze(const Dev &D, const Smem &S, uint32_t g, uint32_t cdl, uint32_t tend,
+                                            uint32_t lfill)
+{
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        S.misc[4] = ng_len(D, g);
+        uint32_t e = atomicAdd(D.epoch, 1u) + 1u;
+        S.misc[5] = e;
+        S.misc[6] = 0u;
+        S.misc[0] = 0u;
+    }
+    cta_sync();
+    if (S.misc[5] == 0u) {
+        // the stamp counter wrapped: clear every stamp, restart at 1
+        for (uint32_t v = tid; v < D.nv; v += nt) D.stamp[v] = 0u;
+        cta_sync();
+        if (tid == 0) { *D.epoch = 1u; S.misc[5] = 1u; }
+        cta_sync();
+    }
+    const uint32_t len = S.misc[4], ep = S.misc[5];
+    for (uint32_t q = tid; q < len; q += nt) {
+        const uint32_t u = ng_lit(D, g, q) >> 1;
+        if (u < D.nv) atomicMax(&S.misc[6], (uint32_t)max(__ldcg(D.dl + u), 0));
+    }
+    cta_sync();
+    const uint32_t m = S.misc[6];
+    if (m <= 1u) {
+        if (tid == 0) S.misc[0] = 1u;
+        cta_sync();
+        return;
+    }
+    const uint32_t seg0 = __ldcg(D.level_start + m);
+    const uint32_t seg1 = m >= cdl ? tend : __ldcg(D.level_start + m + 1u);
+    if (!(seg0 < seg1 && seg1 <= D.nv)) {
+        if (tid == 0) { S.misc[0] = 2u; S.misc[1] = 10u; S.misc[2] = seg0; S.misc[3] = m; }
+        cta_sync();
+        return;
+    }
+    for (uint32_t w = (seg0 >> 5) + tid; w <= ((seg1 - 1u) >> 5); w += nt) D.cand[w] = 0u;
+    cta_sync();
+    if (tid < 32u) {
+        const uint32_t lane = tid;
+        ResState R{m, seg0, seg1, ep, lfill + 1u, 0u, 1u, false, 0u, 0u};
+        uint32_t cnt = res_add_nogood(D, R, g, 0xFFFFFFFFu);
+        __syncwarp();
+        int p = (int)seg1 - 1;
+        const int wlo = (int)(seg0 >> 5);
+        uint32_t uip = 0xFFFFFFFFu;
+        while (!R.err) {
+            // the highest marked position <= p: 32 bitset words per step
+            int q = -1;
+            while (p >= (int)seg0) {
+                const int wtop = p >> 5, w = wtop - (int)lane;
+                uint32_t bits = 0;
+                if (w >= wlo) {
+                    bits = __ldcg(D.cand + w);
+                    if (w == wtop) bits &= (2u << (p & 31)) - 1u;
+                    if (w == wlo) bits &= ~0u << (seg0 & 31u);
+                }
+                const unsigned bal = __ballot_sync(FULL_MASK, bits != 0u);
+                if (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const uint32_t b = __shfl_sync(FULL_MASK, bits, src);
+                    q = (wtop - src) * 32 + 31 - __clz(b);
+                    break;
+                }
+                p = (wtop - 32) * 32 + 31;
+            }
+            if (q < 0) { res_fail(R, 6u, cnt); break; }
+            if (cnt == 0u) { res_fail(R, 7u, (uint32_t)q); break; }
+            const uint32_t entry = __ldcg(D.trail + q), e = entry & TRAIL_VAR;
+            if (e >= D.nv) { res_fail(R, 8u, (uint32_t)q); break; }
+            if (--cnt == 0u) { uip = entry; break; }     // sigma is the only literal at level m
+            const uint32_t r = __ldcg(D.reason + e);
+            if (r < R_INPUT) {
+                cnt += res_add_nogood(D, R, r, e);
+            } else if (r == R_COMPLETE) {
+                cnt += res_add_decisions(D, R, (uint32_t)max(__ldcg(D.dl + e), 0), e);
+            } else {
+                res_fail(R, 9u, e);                       // a decision with others at its level
+                break;
+            }
+            __syncwarp();
+            p = q - 1;
+        }
+        const uint32_t n = 1u + R.nout;
+        if (lane == 0) {
+            if (R.err) {
+                S.misc[0] = 2u;
+                S.misc[1] = R.why;
+                S.misc[2] = R.what;
+                S.misc[3] = m;
+            } else {
+                if (lfill + 1u < D.lits_cap) D.lits[lfill] = mk_lit(uip & TRAIL_VAR, (uip & TRAIL_F) != 0u);
+                if (lfill + n < D.lits_cap) D.lits[lfill + n - 1u] |= END_BIT;
+                S.misc[1] = R.kappa;
+                S.misc[2] = n;
+                S.misc[3] = m;
+            }
+        }
+        __syncwarp();
+        if (!R.err && D.heuristic == 1) {
+            for (uint32_t q = lane; q < n && lfill + q < D.lits_cap; q += 32u) {
+                const uint32_t bv = (D.lits[lfill + q] & ~END_BIT) >> 1;
+                if (bv >= D.na && (bv - D.na) % 3u == 0u) atomicAdd(D.act + (bv - D.na) / 3u, 1u);
+            }
+        }
+    }
+    cta_sync();
+}
+
 __device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase, uint32_t cta)
 {
     View V;
@@ -1346,11 +1604,16 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 }
                 if (cta0) {
                     uint32_t g = (uint32_t)(A.ckey & 0xFFFFFFFFull);
-                    analyze(D, S, g, C.cdl, C.lfill, true);
+                    if (D.learning) res_analyze(D, S, g, C.cdl, tend, C.lfill);
+                    else analyze(D, S, g, C.cdl, C.lfill, true);
                     if (leader) {
                         atomicAdd(&D.stats->conflicts, 1ull);
                         n_conf++;
-                        if (S.misc[0]) {
+                        if (S.misc[0] == 2u) {
+                            N.op = OP_DONE; N.err = -6; N.status = 0;
+                            debug_analysis(D, g, tend, C.lfill, 0u, S.misc[1], S.misc[3]);
+                            D.stats->dbg_lfill = S.misc[2];
+                        } else if (S.misc[0]) {
                             N.op = OP_DONE;
                             N.status = C.n_models > 0 ? 10 : 20;
                         } else {
@@ -1366,6 +1629,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                                 N.tb = tend;
                                 atomicAdd(&D.stats->learned, 1ull);
                                 atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
+                                debug_analysis(D, g, tend, C.lfill, n, S.misc[1], D.learning ? S.misc[3] : 0u);
                             }
                         }
                     }
@@ -1444,6 +1708,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 D.level_start[L] = tend;
                 D.dec_var[L] = bv;
                 D.trail[tend] = bv;
+                if (D.tpos) D.tpos[bv] = tend;
                 D.dl[bv] = (int32_t)L;
                 D.reason[bv] = R_DECISION;
                 uint32_t nw = deps_words(D, L), bit = level_bit(D, L);
@@ -1613,13 +1878,18 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 }
                 cta_sync();
                 const uint32_t lf = C.lfill + len;
-                analyze(D, S, C.conf_id, C.cdl, lf, false);
+                if (D.learning) res_analyze(D, S, C.conf_id, C.cdl, tend, lf);
+                else analyze(D, S, C.conf_id, C.cdl, lf, false);
                 if (leader) {
                     atomicAdd(&D.stats->conflicts, 1ull);
                     n_conf++;
                     atomicAdd(&D.stats->learned, 1ull);
                     atomicAdd(&D.stats->learned_lits, (unsigned long long)len);
-                    if (S.misc[0]) {
+                    if (S.misc[0] == 2u) {
+                        N.op = OP_DONE; N.err = -6; N.status = 0;
+                        debug_analysis(D, C.conf_id, tend, lf, 0u, S.misc[1], S.misc[3]);
+                        D.stats->dbg_lfill = S.misc[2];
+                    } else if (S.misc[0]) {
                         N.op = OP_DONE;
                         N.status = C.n_models > 0 ? 10 : 20;
                         N.n_learned = C.n_learned + 1u;
@@ -1633,6 +1903,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                         N.target = S.misc[1];
                         atomicAdd(&D.stats->learned, 1ull);
                         atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
+                        debug_analysis(D, C.conf_id, tend, lf, n, S.misc[1], D.learning ? S.misc[3] : 0u);
                     }
                 }
             }
