@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--learned", type=int, default=256,
                     help="held-out programs for the learned-heuristic comparison; 0 = skip")
     ap.add_argument("--learned-train", type=int, default=1024, help="training programs (traces)")
+    ap.add_argument("--no-learning-compare", action="store_true",
+                    help="skip the fwd-learning vs first-UIP resolution comparison")
     ap.add_argument("--sweep-only", type=int, default=0,
                     help="profiling aid: load the program and run this many standalone sweeps")
     return ap.parse_args()
@@ -319,6 +321,7 @@ def run_ours(a, rank, world, local_rank):
                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
         batched = _batched(a, aspgpu, torch) if a.batch > 0 else None
         learned = _learned(a, aspgpu, torch) if a.learned > 0 else None
+        learning = None if a.no_learning_compare else _learning(a, aspgpu, prog)
         cpu = None if a.no_cpu else _cpu_baseline(prog, a.cpu_seconds)
         tsec = ms / 1e3
         out = {
@@ -333,7 +336,7 @@ def run_ours(a, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": a.steps,
             "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "batched": batched,
-            "learned_heuristic": learned,
+            "learned_heuristic": learned, "learning_compare": learning,
             "clocks": clk.summary(),
             "search": {"statuses": statuses, "decisions_per_s": totals["decisions"] / tsec,
                        "propagations_per_s": totals["propagations"] / tsec,
@@ -352,6 +355,35 @@ def run_ours(a, rank, world, local_rank):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out, default=_plain), flush=True)
+
+
+def _learning(a, aspgpu, prog):
+    """fwd-learning against resolution to the first UIP (Algorithm 3) on the
+    same programs, budgets and heuristic: device time, rates and learned
+    nogood length of each (the quantities the paper compares)."""
+    from synth.programs import random_program, program_seed
+    cases = [(f"{a.atoms // 1000}k atoms, {a.rules // 1000}k rules (the main workload)", prog, a.conflicts),
+             ("20k atoms, 50k rules, seed (2 << 32) | 1", random_program(20_000, 50_000, program_seed(2, 1)), 1000)]
+    out = []
+    for name, pr, budget in cases:
+        row = {"workload": name, "conflict_budget": budget}
+        for mode, key in ((aspgpu.LEARN_FWD, "fwd"), (aspgpu.LEARN_RES, "res")):
+            P = aspgpu.Program(pr, learning=mode, conflict_budget=budget, time_budget_ms=60_000,
+                               view_mode=a.view, frontier=a.frontier)
+            P.solve(1, cap=1)                      # warm-up solve
+            status, _, _ = P.solve(1, cap=1)
+            s = P.stats()
+            sec = max(s["ns_total"], 1) / 1e9
+            row[key] = {"status": int(status), "device_s": sec, "conflicts": s["conflicts"],
+                        "decisions_per_s": s["decisions"] / sec, "propagations_per_s": s["propagations"] / sec,
+                        "conflicts_per_s": s["conflicts"] / sec, "learned_per_s": s["learned"] / sec,
+                        "learned_avg_len": s["learned_literals"] / max(s["learned"], 1),
+                        "us_per_analysis": s["ns_analysis"] / max(s["conflicts"], 1) / 1e3,
+                        "analysis_share": s["ns_analysis"] / max(s["ns_total"], 1),
+                        "max_level": s["max_level"]}
+            P.close()
+        out.append(row)
+    return out
 
 
 def _batched(a, aspgpu, torch):
