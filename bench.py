@@ -322,6 +322,7 @@ def run_ours(a, rank, world, local_rank):
         batched = _batched(a, aspgpu, torch) if a.batch > 0 else None
         learned = _learned(a, aspgpu, torch) if a.learned > 0 else None
         learning = None if a.no_learning_compare else _learning(a, aspgpu, prog)
+        options = None if a.no_learning_compare or a.learned <= 0 else _search_options(a, aspgpu, torch)
         cpu = None if a.no_cpu else _cpu_baseline(prog, a.cpu_seconds)
         tsec = ms / 1e3
         out = {
@@ -336,7 +337,7 @@ def run_ours(a, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": a.steps,
             "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "batched": batched,
-            "learned_heuristic": learned, "learning_compare": learning,
+            "learned_heuristic": learned, "learning_compare": learning, "search_options": options,
             "clocks": clk.summary(),
             "search": {"statuses": statuses, "decisions_per_s": totals["decisions"] / tsec,
                        "propagations_per_s": totals["propagations"] / tsec,
@@ -496,6 +497,48 @@ def _learned(a, aspgpu, torch):
             "speedup_static_solved_per_s": (out["learned_static"]["solved_per_s"] / out["plain"]["solved_per_s"])
             if out["plain"]["solved"] else None,
             "static_training": sstats}
+
+
+def _search_options(a, aspgpu, torch):
+    """Solved programs within the same per-program conflict budget, batched,
+    under each learning / backjump / restart option, on the held-out set of
+    the learned-heuristic comparison."""
+    import oracle
+    evalp = _a11_programs(a.learned, 2 * 10**6)
+    budget = a.batch_conflicts
+    modes = (("fwd, backjump h-1 (default)", dict()),
+             ("fwd, asserting backjump", dict(backjump=aspgpu.BACKJUMP_ASSERTING)),
+             ("fwd, Luby restarts x16", dict(restart_conflicts=16)),
+             ("res (first UIP)", dict(learning=aspgpu.LEARN_RES)),
+             ("res, Luby restarts x16", dict(learning=aspgpu.LEARN_RES, restart_conflicts=16)))
+    out, ref = {}, None
+    checked = bad = mism = 0
+    for name, kw in modes:
+        P = [aspgpu.Program(p, conflict_budget=budget, time_budget_ms=20_000, deps_levels=1024,
+                            learned_capacity=1 << 20, **kw) for p in evalp]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, nm, models = aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        decided = (st == 10) | (st == 20)
+        if ref is None:
+            ref = st.copy()
+        else:
+            both = decided & ((ref == 10) | (ref == 20))
+            mism += int((st[both] != ref[both]).sum())
+        for i, m in enumerate(models):
+            if len(m):
+                checked += 1
+                bad += not oracle.is_answer_set(evalp[i], m[0])
+        out[name] = {"seconds": dt, "solved": int(decided.sum()), "solved_per_s": int(decided.sum()) / dt,
+                     "conflicts": int(sum(q.stats()["conflicts"] for q in P)),
+                     "restarts": int(sum(q.stats()["restarts"] for q in P))}
+        for q in P:
+            q.close()
+    return {"workload": f"{a.learned} held-out programs of the learned-heuristic comparison, conflict "
+                        f"budget {budget}, batched", "modes": out, "status_mismatches": mism,
+            "models_checked": checked, "invalid_models": bad}
 
 
 def run_sweeps(a):

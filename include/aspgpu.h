@@ -84,6 +84,14 @@ extern "C" {
 #define ASP_LEARN_FWD 0
 #define ASP_LEARN_RES 1
 
+/* Backjump target of fwd-learning, with h the highest level in the
+ * conflict's dependency bitmap.  H_MINUS_1: level h-1 (Algorithm 4's
+ * reading).  ASSERTING: the second-highest level in the bitmap (1 if there
+ * is none), where the learned nogood is already unit; it can jump further.
+ * An overflowed bitmap (levels beyond deps_levels) always goes to h-1. */
+#define ASP_BACKJUMP_H_MINUS_1 0
+#define ASP_BACKJUMP_ASSERTING 1
+
 #define ASP_MLP_FEATURES 16   /* inputs of the learned heuristic per candidate rule */
 #define ASP_MLP_PARAMS 1153   /* W1[64][16], b1[64], w2[64], b2 */
 
@@ -120,6 +128,15 @@ typedef struct {
     int32_t frontier;
     /* ASP_LEARN_*: conflict analysis */
     int32_t learning;
+    /* ASP_BACKJUMP_*: target of fwd-learning's backjump (resolution
+       learning always backjumps to its asserting level) */
+    int32_t backjump;
+    /* Luby restarts (not in the paper's experiments): after the i-th
+       restart, restart again once luby(i+1) x restart_conflicts nogoods
+       have been learned (1 1 2 1 1 2 4 ...) -- the backjump after that
+       learned nogood goes to the root instead of its target; learned
+       nogoods are kept.  0 = no restarts */
+    int32_t restart_conflicts;
 } asp_options;
 
 typedef struct {
@@ -139,6 +156,7 @@ typedef struct {
                                                    asp_solve_batch */
     int64_t ns_slowest_cta, ns_slowest_sweep;   /* sums over phases of the slowest CTA's time
                                                    before the phase barrier, and in the sweep */
+    int64_t restarts;                           /* restarts (asp_options.restart_conflicts) */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */

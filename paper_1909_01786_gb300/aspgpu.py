@@ -21,6 +21,7 @@ HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED = 0, 1, 2
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 VIEW_AUTO, VIEW_PLAIN, VIEW_PACKED, VIEW_BYTES = 0, 1, 2, 3
 LEARN_FWD, LEARN_RES = 0, 1
+BACKJUMP_H_MINUS_1, BACKJUMP_ASSERTING = 0, 1
 R_DECISION, R_COMPLETE, R_INPUT = 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD
 
 _lib = None
@@ -40,7 +41,8 @@ class Options(C.Structure):
                 ("block_threads", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
                 ("mlp_weights", C.c_void_p), ("trace_capacity", C.c_int64),
-                ("view_mode", C.c_int32), ("frontier", C.c_int32), ("learning", C.c_int32)]
+                ("view_mode", C.c_int32), ("frontier", C.c_int32), ("learning", C.c_int32),
+                ("backjump", C.c_int32), ("restart_conflicts", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -50,7 +52,8 @@ class Stats(C.Structure):
         "propagations", "conflicts", "decisions", "completions", "learned",
         "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
         "ns_sweep", "ns_analysis", "ns_decision", "ns_stability", "ns_buckets", "ns_learned",
-        "ns_barrier", "view_mode", "batch_view_mode", "ns_slowest_cta", "ns_slowest_sweep")]
+        "ns_barrier", "view_mode", "batch_view_mode", "ns_slowest_cta", "ns_slowest_sweep",
+        "restarts")]
 
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
@@ -160,7 +163,8 @@ class Program:
 
     def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
                  learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True,
-                 mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False, learning=LEARN_FWD):
+                 mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False, learning=LEARN_FWD,
+                 backjump=BACKJUMP_H_MINUS_1, restart_conflicts=0):
         L = lib()
         self.n_atoms = int(prog.n_atoms)
         self._keep = []
@@ -175,6 +179,8 @@ class Program:
         opt.view_mode = int(view_mode)
         opt.frontier = 1 if frontier else 0
         opt.learning = int(learning)
+        opt.backjump = int(backjump)
+        opt.restart_conflicts = int(restart_conflicts)
         opt.heuristic, opt.deps_levels = heuristic, deps_levels
         opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
         opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads

@@ -463,6 +463,12 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     if (D.heuristic > 3) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
     if (p->opt.learning < 0 || p->opt.learning > 1) { delete p; return fail(ASP_E_ARG, "unknown learning"); }
     D.learning = (uint32_t)p->opt.learning;
+    if (p->opt.backjump < 0 || p->opt.backjump > 1 || p->opt.restart_conflicts < 0) {
+        delete p;
+        return fail(ASP_E_ARG, "unknown backjump or negative restart_conflicts");
+    }
+    D.backjump = (uint32_t)p->opt.backjump;
+    D.restart_unit = (uint32_t)p->opt.restart_conflicts;
     p->n_nogoods = H.n_nogoods;
     p->n_literals = H.n_literals;
     p->n_units = (int64_t)H.units.size();
@@ -655,6 +661,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
     o.view_mode = D.view_mode; o.batch_view_mode = p->D1[0].view_mode;
     o.ns_slowest_cta = (int64_t)s.ns_slowest; o.ns_slowest_sweep = (int64_t)s.ns_slowest_sweep;
+    o.restarts = (int64_t)s.restarts;
 }
 
 extern "C" {

@@ -89,6 +89,7 @@ struct DevStats {
     unsigned long long ns_buckets, ns_learned, ns_barrier, pad2;
     // sums over phases of the slowest CTA's busy time and sweep time
     unsigned long long ns_slowest, ns_slowest_sweep;
+    unsigned long long restarts;
     unsigned int trace_n, pad4;    // trace records written (atomic)
     // the last conflict analysis: conflicting nogood, trail length (claims of
     // the conflict round included), learned nogood id and length, backjump
@@ -108,6 +109,11 @@ struct Dev {
     uint32_t bk_base[16], bk_n[16];
     uint32_t lits_static, lits_cap, learned_ng_cap, pad0;
     uint32_t WW, Wlevels, mode, heuristic;
+    // fwd-learning backjump: 0 to h-1 (h = highest level of the conflict's
+    // bitmap), 1 to the second-highest level (the asserting level);
+    // restart_unit: Luby restarts every luby(i) x restart_unit learned
+    // nogoods (0 = none)
+    uint32_t backjump, restart_unit;
     // static partition of the buckets over the CTAs by groups (atoms and
     // their rules; constraints): CTA g owns nogoods [cta_boff[L*(G+1)+g],
     // cta_boff[L*(G+1)+g+1]) of bucket L, and keeps in shared memory the

@@ -1184,6 +1184,18 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
             uint32_t h = overflow ? cdl : (uint32_t)top + 1u;
             S.misc[0] = 0;
             S.misc[1] = h - 1u;
+            if (D.backjump == 1u && !overflow) {
+                // the asserting level: the second-highest level of the bitmap
+                // (1 if h is its only level); the learned nogood is unit there
+                int second = -1;
+                for (int w = top >> 6; w >= 0 && second < 0; w--) {
+                    unsigned long long m = S.bm[w];
+                    if (w == (int)D.WW - 1) m &= ~(1ull << 63);
+                    if (w == (top >> 6)) m &= (1ull << (top & 63)) - 1ull;
+                    if (m) second = w * 64 + 63 - __clzll((long long)m);
+                }
+                S.misc[1] = second >= 1 ? (uint32_t)second + 1u : 1u;
+            }
             // write the decision literals, levels ascending
             uint32_t n = 0;
             for (uint32_t w = 0; w < nw; w++) {
@@ -1497,6 +1509,19 @@ __device__ __forceinline__ Smem make_smem(const Dev &D, unsigned long long *raw)
     return S;
 }
 
+// The i-th term (i >= 1) of the Luby sequence 1 1 2 1 1 2 4 1 1 2 ...: 2^(k-1)
+// if i = 2^k - 1, else the term at i - 2^(k-1) + 1 for the k with
+// 2^(k-1) <= i < 2^k - 1 (Luby, Sinclair and Zuckerman's restart schedule).
+__device__ __forceinline__ uint32_t luby(uint32_t i)
+{
+    for (;;) {
+        uint32_t k = 1;
+        while (k < 31u && (1u << k) - 1u < i) k++;
+        if ((1u << k) - 1u == i || k == 31u) return 1u << (k - 1u);
+        i = i - (1u << (k - 1u)) + 1u;
+    }
+}
+
 // Phase barrier of the solving group: the whole grid (one program on every
 // SM) or one CTA (one program of a batch).
 template <bool BATCH>
@@ -1524,10 +1549,14 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     // written to the stats when the search ends
     __shared__ unsigned long long t_start, t_phase, n_conf, n_phases, ns_bar, ns_sw, ns_an, ns_de, ns_st;
     __shared__ unsigned long long ns_slow, ns_slow_sw, t_cta0;
+    // restarts: learned nogoods since the last restart, restarts so far
+    __shared__ uint32_t r_conf, r_idx;
     if (leader) {
         t_start = globaltimer_ns();
         t_phase = t_start;
         n_conf = n_phases = ns_bar = ns_sw = ns_an = ns_de = ns_st = ns_slow = ns_slow_sw = 0ull;
+        r_conf = 0u;
+        r_idx = 0u;
     }
     if (threadIdx.x == 0) { s_tlearned = 0ull; s_tbuckets = 0ull; t_cta0 = globaltimer_ns(); }
 
@@ -1630,6 +1659,12 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                                 atomicAdd(&D.stats->learned, 1ull);
                                 atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
                                 debug_analysis(D, g, tend, C.lfill, n, S.misc[1], D.learning ? S.misc[3] : 0u);
+                                if (D.restart_unit && ++r_conf >= luby(r_idx + 1u) * D.restart_unit) {
+                                    r_conf = 0u;
+                                    r_idx++;
+                                    N.target = 1u;
+                                    atomicAdd(&D.stats->restarts, 1ull);
+                                }
                             }
                         }
                     }
@@ -1904,6 +1939,12 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                         atomicAdd(&D.stats->learned, 1ull);
                         atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
                         debug_analysis(D, C.conf_id, tend, lf, n, S.misc[1], D.learning ? S.misc[3] : 0u);
+                        if (D.restart_unit && ++r_conf >= luby(r_idx + 1u) * D.restart_unit) {
+                            r_conf = 0u;
+                            r_idx++;
+                            N.target = 1u;
+                            atomicAdd(&D.stats->restarts, 1ull);
+                        }
                     }
                 }
             }
