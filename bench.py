@@ -509,6 +509,7 @@ def _search_options(a, aspgpu, torch):
     modes = (("fwd, backjump h-1 (default)", dict()),
              ("fwd, asserting backjump", dict(backjump=aspgpu.BACKJUMP_ASSERTING)),
              ("fwd, Luby restarts x16", dict(restart_conflicts=16)),
+             ("fwd, 4 conflicts per round", dict(conflicts_per_round=4)),
              ("res (first UIP)", dict(learning=aspgpu.LEARN_RES)),
              ("res, Luby restarts x16", dict(learning=aspgpu.LEARN_RES, restart_conflicts=16)))
     out, ref = {}, None

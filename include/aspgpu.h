@@ -137,6 +137,11 @@ typedef struct {
        learned nogood goes to the root instead of its target; learned
        nogoods are kept.  0 = no restarts */
     int32_t restart_conflicts;
+    /* conflicts analysed when a round finds several (Section 4.2 allows
+       one or more): 1..4, 0 = 1.  The shortest conflicting nogood, then the
+       shortest of each class of nogood ids mod 3, shorter first; each gives
+       a learned nogood and the search backjumps to the lowest target */
+    int32_t conflicts_per_round;
 } asp_options;
 
 typedef struct {
@@ -157,6 +162,8 @@ typedef struct {
     int64_t ns_slowest_cta, ns_slowest_sweep;   /* sums over phases of the slowest CTA's time
                                                    before the phase barrier, and in the sweep */
     int64_t restarts;                           /* restarts (asp_options.restart_conflicts) */
+    int64_t conflict_rounds;                    /* rounds that found a conflict; conflicts
+                                                   counts every analysed one */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */

@@ -42,7 +42,8 @@ class Options(C.Structure):
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
                 ("mlp_weights", C.c_void_p), ("trace_capacity", C.c_int64),
                 ("view_mode", C.c_int32), ("frontier", C.c_int32), ("learning", C.c_int32),
-                ("backjump", C.c_int32), ("restart_conflicts", C.c_int32)]
+                ("backjump", C.c_int32), ("restart_conflicts", C.c_int32),
+                ("conflicts_per_round", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -53,7 +54,7 @@ class Stats(C.Structure):
         "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
         "ns_sweep", "ns_analysis", "ns_decision", "ns_stability", "ns_buckets", "ns_learned",
         "ns_barrier", "view_mode", "batch_view_mode", "ns_slowest_cta", "ns_slowest_sweep",
-        "restarts")]
+        "restarts", "conflict_rounds")]
 
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
@@ -164,7 +165,7 @@ class Program:
     def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
                  learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True,
                  mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False, learning=LEARN_FWD,
-                 backjump=BACKJUMP_H_MINUS_1, restart_conflicts=0):
+                 backjump=BACKJUMP_H_MINUS_1, restart_conflicts=0, conflicts_per_round=1):
         L = lib()
         self.n_atoms = int(prog.n_atoms)
         self._keep = []
@@ -181,6 +182,7 @@ class Program:
         opt.learning = int(learning)
         opt.backjump = int(backjump)
         opt.restart_conflicts = int(restart_conflicts)
+        opt.conflicts_per_round = int(conflicts_per_round)
         opt.heuristic, opt.deps_levels = heuristic, deps_levels
         opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
         opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads

@@ -469,6 +469,11 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     }
     D.backjump = (uint32_t)p->opt.backjump;
     D.restart_unit = (uint32_t)p->opt.restart_conflicts;
+    if (p->opt.conflicts_per_round < 0 || p->opt.conflicts_per_round > 4) {
+        delete p;
+        return fail(ASP_E_ARG, "conflicts_per_round must be 0..4");
+    }
+    D.conf_per_round = (uint32_t)std::max(1, p->opt.conflicts_per_round);
     p->n_nogoods = H.n_nogoods;
     p->n_literals = H.n_literals;
     p->n_units = (int64_t)H.units.size();
@@ -629,7 +634,7 @@ static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t m
     ctl[0].tb = n_input;
     ctl[0].lfill = D.lits_static;
     for (int i = 0; i < 4; i++) {
-        acc[i].ckey = NO_KEY; acc[i].dkey = 0; acc[i].nclaim = 0; acc[i].flag = 0;
+        acc[i].ckey = NO_KEY; acc[i].cslot[0] = acc[i].cslot[1] = acc[i].cslot[2] = NO_KEY; acc[i].dkey = 0; acc[i].nclaim = 0; acc[i].flag = 0;
         acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0; acc[i].tbusy = 0; acc[i].tsweep = 0;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
@@ -661,7 +666,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
     o.view_mode = D.view_mode; o.batch_view_mode = p->D1[0].view_mode;
     o.ns_slowest_cta = (int64_t)s.ns_slowest; o.ns_slowest_sweep = (int64_t)s.ns_slowest_sweep;
-    o.restarts = (int64_t)s.restarts;
+    o.restarts = (int64_t)s.restarts; o.conflict_rounds = (int64_t)s.conflict_rounds;
 }
 
 extern "C" {
@@ -793,7 +798,8 @@ int asp_sweep(asp_prog *p, int32_t passes)
 {
     if (!p || passes < 1) return fail(ASP_E_ARG, "bad argument");
     Acc a;
-    a.ckey = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+    a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY;
+    a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
     a.tbusy = 0; a.tsweep = 0;
     cudaError_t e = cudaMemcpyAsync(p->d_sweep_acc, &a, sizeof(a), cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep reset");

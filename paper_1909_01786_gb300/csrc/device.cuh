@@ -69,6 +69,8 @@ struct Ctl {              // double-buffered control block (phase parity)
 
 struct Acc {              // per-phase accumulators, indexed by phase % 4
     unsigned long long ckey;    // min over conflicts of (length << 32 | nogood id)
+    unsigned long long cslot[3]; // the same over conflicts with id % 3 == 0, 1, 2 (several
+                                 // conflicts per round)
     unsigned long long dkey;    // max over candidate rules of (score << 32 | ~j)
     uint32_t nclaim;            // variables claimed in the phase
     uint32_t flag;              // something changed (least-model iteration)
@@ -89,7 +91,7 @@ struct DevStats {
     unsigned long long ns_buckets, ns_learned, ns_barrier, pad2;
     // sums over phases of the slowest CTA's busy time and sweep time
     unsigned long long ns_slowest, ns_slowest_sweep;
-    unsigned long long restarts;
+    unsigned long long restarts, conflict_rounds;
     unsigned int trace_n, pad4;    // trace records written (atomic)
     // the last conflict analysis: conflicting nogood, trail length (claims of
     // the conflict round included), learned nogood id and length, backjump
@@ -114,6 +116,9 @@ struct Dev {
     // restart_unit: Luby restarts every luby(i) x restart_unit learned
     // nogoods (0 = none)
     uint32_t backjump, restart_unit;
+    // conflicts analysed per conflicting round (1..4): the shortest, then
+    // the shortest of each class id % 3; the lowest target wins
+    uint32_t conf_per_round, pad2;
     // static partition of the buckets over the CTAs by groups (atoms and
     // their rules; constraints): CTA g owns nogoods [cta_boff[L*(G+1)+g],
     // cta_boff[L*(G+1)+g+1]) of bucket L, and keeps in shared memory the

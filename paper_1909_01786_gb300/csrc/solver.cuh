@@ -345,7 +345,9 @@ __shared__ unsigned long long s_tlearned, s_tbuckets;
 
 __device__ __forceinline__ void report_conflict(const SweepCtx &X, uint32_t id, uint32_t len)
 {
-    atomicMin(&X.acc->ckey, ((unsigned long long)len << 32) | id);
+    const unsigned long long key = ((unsigned long long)len << 32) | id;
+    atomicMin(&X.acc->ckey, key);
+    atomicMin(&X.acc->cslot[id % 3u], key);    // read only with several conflicts per round
 }
 
 // Record a won claim: trail slot, level, reason.
@@ -1632,41 +1634,71 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     break;
                 }
                 if (cta0) {
-                    uint32_t g = (uint32_t)(A.ckey & 0xFFFFFFFFull);
-                    if (D.learning) res_analyze(D, S, g, C.cdl, tend, C.lfill);
-                    else analyze(D, S, g, C.cdl, C.lfill, true);
+                    // the conflicts to analyse: the shortest one, then (several
+                    // per round) the shortest of each id class, shorter first
+                    __shared__ unsigned long long s_keys[4];
+                    __shared__ uint32_t s_nk, s_stop;
                     if (leader) {
-                        atomicAdd(&D.stats->conflicts, 1ull);
-                        n_conf++;
-                        if (S.misc[0] == 2u) {
-                            N.op = OP_DONE; N.err = -6; N.status = 0;
-                            debug_analysis(D, g, tend, C.lfill, 0u, S.misc[1], S.misc[3]);
-                            D.stats->dbg_lfill = S.misc[2];
-                        } else if (S.misc[0]) {
-                            N.op = OP_DONE;
-                            N.status = C.n_models > 0 ? 10 : 20;
-                        } else {
-                            uint32_t n = S.misc[2];
-                            if (C.lfill + n + 64u >= D.lits_cap || C.n_learned + 1u >= D.learned_ng_cap) {
+                        uint32_t nk = 0;
+                        s_keys[nk++] = A.ckey;
+                        for (int j = 0; j < 3; j++) {
+                            unsigned long long key = A.cslot[j];
+                            if (key == NO_KEY || key == A.ckey) continue;
+                            uint32_t i = nk++;
+                            while (i > 1u && s_keys[i - 1u] > key) { s_keys[i] = s_keys[i - 1u]; i--; }
+                            s_keys[i] = key;
+                        }
+                        s_nk = min(nk, max(D.conf_per_round, 1u));
+                        s_stop = 0u;
+                        atomicAdd(&D.stats->conflict_rounds, 1ull);
+                        N.target = 0xFFFFFFFFu;
+                    }
+                    cta_sync();
+                    const uint32_t nk = s_nk;
+                    for (uint32_t c = 0; c < nk; c++) {
+                        const uint32_t g = (uint32_t)(s_keys[c] & 0xFFFFFFFFull);
+                        const uint32_t lf = N.lfill;
+                        if (D.learning) res_analyze(D, S, g, C.cdl, tend, lf);
+                        else analyze(D, S, g, C.cdl, lf, true);
+                        if (leader) {
+                            atomicAdd(&D.stats->conflicts, 1ull);
+                            n_conf++;
+                            if (S.misc[0] == 2u) {
                                 N.op = OP_DONE; N.err = -6; N.status = 0;
+                                debug_analysis(D, g, tend, lf, 0u, S.misc[1], S.misc[3]);
+                                D.stats->dbg_lfill = S.misc[2];
+                                s_stop = 1u;
+                            } else if (S.misc[0]) {
+                                N.op = OP_DONE;
+                                N.status = C.n_models > 0 ? 10 : 20;
+                                s_stop = 1u;
                             } else {
-                                D.learned_ids[C.n_learned] = C.lfill;
-                                N.n_learned = C.n_learned + 1u;
-                                N.lfill = C.lfill + n;
-                                N.op = OP_BACKJUMP;
-                                N.target = S.misc[1];
-                                N.tb = tend;
-                                atomicAdd(&D.stats->learned, 1ull);
-                                atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
-                                debug_analysis(D, g, tend, C.lfill, n, S.misc[1], D.learning ? S.misc[3] : 0u);
-                                if (D.restart_unit && ++r_conf >= luby(r_idx + 1u) * D.restart_unit) {
-                                    r_conf = 0u;
-                                    r_idx++;
-                                    N.target = 1u;
-                                    atomicAdd(&D.stats->restarts, 1ull);
+                                uint32_t n = S.misc[2];
+                                if (lf + n + 64u >= D.lits_cap || N.n_learned + 1u >= D.learned_ng_cap) {
+                                    N.op = OP_DONE; N.err = -6; N.status = 0;
+                                    s_stop = 1u;
+                                } else {
+                                    D.learned_ids[N.n_learned] = lf;
+                                    N.n_learned = N.n_learned + 1u;
+                                    N.lfill = lf + n;
+                                    N.op = OP_BACKJUMP;
+                                    N.target = min(N.target, S.misc[1]);
+                                    N.tb = tend;
+                                    atomicAdd(&D.stats->learned, 1ull);
+                                    atomicAdd(&D.stats->learned_lits, (unsigned long long)n);
+                                    debug_analysis(D, g, tend, lf, n, S.misc[1], D.learning ? S.misc[3] : 0u);
                                 }
                             }
                         }
+                        cta_sync();
+                        if (s_stop) break;
+                    }
+                    if (leader && N.op == OP_BACKJUMP && D.restart_unit &&
+                        ++r_conf >= luby(r_idx + 1u) * D.restart_unit) {
+                        r_conf = 0u;
+                        r_idx++;
+                        N.target = 1u;
+                        atomicAdd(&D.stats->restarts, 1ull);
                     }
                 }
                 break;
@@ -1970,7 +2002,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             D.ctl[(k + 1u) & 1u] = N;
             Acc z;
-            z.ckey = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0;
+            z.ckey = NO_KEY; z.cslot[0] = z.cslot[1] = z.cslot[2] = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0;
             z.tbusy = 0; z.tsweep = 0;
             D.acc[(k + 1u) & 3u] = z;
             // fold long-nogood checks of the previous phase into the stats

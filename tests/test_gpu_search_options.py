@@ -119,3 +119,69 @@ def test_bad_options_are_rejected(gpu):
         gpu.Program(tiny_program(1), backjump=5)
     with pytest.raises(gpu.AspError):
         gpu.Program(tiny_program(1), restart_conflicts=-1)
+
+
+# ---- several conflicts per round (Section 4.2: "one or more" conflicts)
+
+@pytest.mark.parametrize("index", [3, 77, 151, 402, 555, 918])
+@pytest.mark.parametrize("learning", [0, 1])
+def test_tiny_full_enumeration_several_conflicts(gpu, index, learning):
+    prog = tiny_program(index)
+    want = _sets(oracle.brute_force(prog))
+    P = gpu.Program(prog, conflicts_per_round=4, learning=learning)
+    status, models, n = P.solve(0, cap=1 << 12)
+    assert _sets(models) == want and n == len(want)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("learning,backjump,restarts", [(0, 0, 0), (1, 0, 0), (0, 1, 8)])
+def test_search_answers_several_conflicts(gpu, seed, learning, backjump, restarts):
+    prog = random_program(600 + 200 * seed, 1400 + 400 * seed, program_seed(804, seed))
+    ost, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=30)
+    assert ost in (oracle.SAT, oracle.UNSAT)
+    P = gpu.Program(prog, conflicts_per_round=4, learning=learning, backjump=backjump,
+                    restart_conflicts=restarts, time_budget_ms=60_000)
+    st, models, _ = P.solve(1, cap=1)
+    assert st == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT)
+    for m in models:
+        assert oracle.is_answer_set(prog, m)
+
+
+def test_several_conflicts_are_analysed(gpu):
+    """With one conflict per round every conflicting round is one analysis;
+    with up to four, some rounds analyse more (each learns a nogood)."""
+    tot = {1: [0, 0], 4: [0, 0]}
+    for seed in range(4):
+        prog = random_program(20000, 50000, program_seed(805, seed))
+        for cpr in (1, 4):
+            P = gpu.Program(prog, conflicts_per_round=cpr, conflict_budget=60, time_budget_ms=60_000)
+            status, _, _ = P.solve(1, cap=1)
+            s = P.stats()
+            if status == gpu.UNSAT:
+                continue          # a final conflict at the root is counted outside rounds
+            c = s["conflicts"] - s["loop_nogoods"]     # loop nogoods are analysed outside rounds
+            tot[cpr][0] += c
+            tot[cpr][1] += s["conflict_rounds"]
+            if cpr == 1:
+                assert c == s["conflict_rounds"]
+            assert s["conflict_rounds"] <= c <= cpr * s["conflict_rounds"]
+    assert tot[4][0] > tot[4][1]
+
+
+@pytest.mark.parametrize("k", [3, 10, 30])
+def test_last_analysis_of_a_round_equals_the_oracle(gpu, k):
+    """Resolution learning with several conflicts per round: the round's last
+    analysis (run on the same state as the others) against the oracle."""
+    from test_gpu_learning import _check_conflict
+    prog = random_program(5000, 12000, program_seed(806, k))
+    P = gpu.Program(prog, conflicts_per_round=4, learning=gpu.LEARN_RES, conflict_budget=k,
+                    time_budget_ms=60_000)
+    status, _, _ = P.solve(1, cap=1)
+    if status != gpu.UNKNOWN or P.stats()["conflicts"] < k:
+        pytest.skip("search ended before the k-th conflict")
+    _check_conflict(gpu, P)
+
+
+def test_bad_conflicts_per_round_is_rejected(gpu):
+    with pytest.raises(gpu.AspError):
+        gpu.Program(tiny_program(1), conflicts_per_round=5)
