@@ -114,6 +114,21 @@ def _dominators(S, m, conflict_vars):
     return dom
 
 
+def _another_order(S, rng):
+    """Trail positions of a random topological order of the implication
+    graph, level by level."""
+    depth = {}
+    for v in S.trail:                                   # antecedents come first
+        a = S.ante[v]
+        ps = [] if a is None else [u for (u, _) in S.ng[a] if u != v and S.level[u] == S.level[v]]
+        depth[v] = 1 + max([depth[u] for u in ps], default=-1)
+    key = {v: (int(S.level[v]), depth[v], float(rng.random())) for v in S.trail}
+    pos = np.full(S.nv, -1, np.int64)
+    for i, v in enumerate(sorted(S.trail, key=lambda v: key[v])):
+        pos[v] = i
+    return pos
+
+
 def _supported_models(prog, nv):
     na = prog.n_atoms
     out = []
@@ -165,6 +180,13 @@ def _search(prog, models, rng):
             assert kappa == max([int(S.level[u]) for (u, _) in d if (u, _) != uip] + [0])
             dom = _dominators(S, m, [u for (u, _) in S.ng[g] if S.level[u] == m])
             assert uip[0] == max(dom, key=lambda u: S.pos[u])
+            # (d) the same result under another trail order that respects
+            # the implication graph (concurrent claims may land in any such
+            # order): levels first, then depth below the level's sources,
+            # random among equals
+            d2, k2, u2 = oracle.first_uip(S.ng[g], _another_order(S, rng), S.level,
+                                          lambda u: None if S.ante[u] is None else S.ng[S.ante[u]])
+            assert (d2, k2, u2) == (d, kappa, uip)
             # (c) no supported model violates it
             for M in models:
                 assert not all(M[u] == (-1 if f else 1) for (u, f) in d)
