@@ -10,7 +10,8 @@
  * and solved by conflict-driven nogood learning with ASP-computation
  * decisions (Section 2; Algorithm 1): propagation and checking of all
  * nogoods to a fixpoint (Section 4.1), conflict analysis from decision-level
- * dependency bitmaps (Section 4.2, Algorithm 4), backjumping, decisions, and
+ * dependency bitmaps (Section 4.2, Algorithm 4) or, as an option, by
+ * resolution to the first UIP (Algorithm 3), backjumping, decisions, and
  * completion of the assignment.  Every step runs in this library's CUDA
  * kernels; the host only builds the nogood store and reads results.
  *
@@ -45,7 +46,8 @@ extern "C" {
 #define ASP_E_OOM (-3)       /* device allocation failed */
 #define ASP_E_CUDA (-4)      /* CUDA runtime error */
 #define ASP_E_CAPACITY (-5)  /* caller's model buffer full; the models found so far are valid */
-#define ASP_E_DEVICE (-6)    /* device-side error: learned-store overflow or barrier timeout */
+#define ASP_E_DEVICE (-6)    /* device-side error: learned-store overflow, barrier timeout, or
+                                an inconsistent state met by resolution learning */
 #define ASP_E_NODEVICE (-7)  /* no CUDA device / compiled kernels unavailable */
 
 #define ASP_STATUS_UNKNOWN 0 /* budget exhausted before the answer was known */

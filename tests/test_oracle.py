@@ -107,7 +107,7 @@ def test_cdnl_equals_brute_force_small(seed):
     assert status == (oracle.SAT if bf else oracle.UNSAT)
 
 
-@pytest.mark.parametrize("index", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("index", list(range(6)) + list(range(100, 2400, 100)))
 def test_cdnl_equals_brute_force_tiny_config(index):
     prog = tiny_program(index)
     bf = _as_sets(oracle.brute_force(prog))
@@ -280,3 +280,10 @@ def test_c8_needs_stability_check():
     assert not oracle.is_answer_set(prog, np.array([1, 1], np.uint8))
     status, models, _ = oracle.cdnl(prog)
     assert status == oracle.UNSAT and len(models) == 0
+
+
+def test_crosscheck_script_on_a_slice():
+    """The committed O2-vs-O1 cross-check (run on 10^4 programs offline)
+    passes on a slice of the same family."""
+    from oracle import crosscheck
+    assert crosscheck.main(["--count", "12", "--first", "9000", "--workers", "2"]) == 0
