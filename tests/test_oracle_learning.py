@@ -114,6 +114,35 @@ def _dominators(S, m, conflict_vars):
     return dom
 
 
+def _wave_first_uip(delta, pos, level, ng, ante, w):
+    """Resolution in waves: with cnt literals of the conflict level marked,
+    resolve the min(cnt - 1, w) highest at once (their reasons' literals
+    join; a variable is taken once); stop at one marked literal."""
+    m = max(level[v] for (v, _) in delta)
+    seen, marked, low = set(), {}, set()
+
+    def add(lits, skip):
+        for (v, f) in lits:
+            if v == skip or v in seen or level[v] <= 0:
+                continue
+            seen.add(v)
+            if level[v] == m:
+                marked[v] = (v, f)
+            else:
+                low.add((v, f))
+
+    add(delta, None)
+    while len(marked) > 1:
+        top = sorted(marked, key=lambda v: -pos[v])[:min(len(marked) - 1, w)]
+        for v in top:
+            del marked[v]
+        for v in top:
+            add(ng[ante[v]], v)
+    (uip,) = marked.values()
+    kappa = max([level[v] for (v, _) in low] + [0])
+    return low | {uip}, kappa, uip
+
+
 def _another_order(S, rng):
     """Trail positions of a random topological order of the implication
     graph, level by level."""
@@ -187,6 +216,10 @@ def _search(prog, models, rng):
             d2, k2, u2 = oracle.first_uip(S.ng[g], _another_order(S, rng), S.level,
                                           lambda u: None if S.ante[u] is None else S.ng[S.ante[u]])
             assert (d2, k2, u2) == (d, kappa, uip)
+            # (e) resolving up to w of the highest marked literals at once,
+            # never the lowest, reaches the same nogood
+            for w in (2, 5, 32):
+                assert _wave_first_uip(S.ng[g], S.pos, S.level, S.ng, S.ante, w) == (d, kappa, uip)
             # (c) no supported model violates it
             for M in models:
                 assert not all(M[u] == (-1 if f else 1) for (u, f) in d)
