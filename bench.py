@@ -300,6 +300,9 @@ def run_ours(a, rank, world, local_rank):
              "note": (f"store of {st['store_bytes'] / 1e6:.0f} MB "
                       + ("is L2-resident (< 126 MB L2)" if st["store_bytes"] < 126e6 else "streams from DRAM every pass"))}
 
+    # every rank solves its block of the batched workload (all ranks reach
+    # the aggregation together, before rank 0's own sections)
+    batched = _batched(a, aspgpu, torch, rank, world, dev) if a.batch > 0 else None
     out = None
     if rank == 0:
         e2e = None
@@ -319,7 +322,6 @@ def run_ours(a, rank, world, local_rank):
             d2h = words * 8 + 32
             e2e = {"value": e2e_checks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
-        batched = _batched(a, aspgpu, torch) if a.batch > 0 else None
         learned = _learned(a, aspgpu, torch) if a.learned > 0 else None
         learning = None if a.no_learning_compare else _learning(a, aspgpu, prog)
         options = None if a.no_learning_compare or a.learned <= 0 else _search_options(a, aspgpu, torch)
@@ -387,47 +389,67 @@ def _learning(a, aspgpu, prog):
     return out
 
 
-def _batched(a, aspgpu, torch):
+def shard_bounds(count, rank, world):
+    """Rank `rank`'s contiguous block [lo, hi) of `count` independent programs
+    (sizes are drawn i.i.d., so blocks are alike); blocks differ by at most one."""
+    base, extra = divmod(count, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
     """Batched vs plain on the same programs: 4 rules per atom, atom counts
     log-uniform in [200, 20000], seeds (4 << 32) | i; per-program conflict
-    budget.  solved = SAT or UNSAT within the budget."""
+    budget.  solved = SAT or UNSAT within the budget.  Under N ranks each
+    rank solves its own block of the programs (no exchange of data); the
+    job reports all ranks' solved programs over the slowest rank's time."""
     from synth.programs import batch_programs
-    progs = batch_programs(a.batch, rules_per_atom=4, config_id=4)
+    lo, hi = shard_bounds(a.batch, rank, world)
+    progs = batch_programs(hi - lo, rules_per_atom=4, config_id=4, first_index=lo) if hi > lo else []
     kw = dict(conflict_budget=a.batch_conflicts, time_budget_ms=20_000, deps_levels=1024,
               learned_capacity=1 << 20)
     P = [aspgpu.Program(p, **kw) for p in progs]
-    # autotuned configuration, launch captured in a CUDA graph; the timed
-    # region replays it once
-    t0 = time.perf_counter()
-    plan = aspgpu.BatchPlan(P, max_models_each=1, cap_each=1, config=aspgpu.BATCH_AUTOTUNE)
-    t_prepare = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, nm, _ = plan.run()
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    info = plan.info()
-    plan.close()
-    solved_b = int(((st == 10) | (st == 20)).sum())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    solved_p = 0
-    agree = 0
-    for i, q in enumerate(P):
-        s_, _, _ = q.solve(1, cap=1)
-        solved_p += s_ in (10, 20)
-        agree += int((s_ in (10, 20)) and (int(st[i]) in (10, 20)) and (s_ == int(st[i])))
-    torch.cuda.synchronize()
-    tp = time.perf_counter() - t0
-    for q in P:
-        q.close()
+    solved_b = solved_p = agree = 0
+    tb = tp = t_prepare = 0.0
+    info = None
+    if P:
+        # autotuned configuration, launch captured in a CUDA graph; the timed
+        # region replays it once
+        t0 = time.perf_counter()
+        plan = aspgpu.BatchPlan(P, max_models_each=1, cap_each=1, config=aspgpu.BATCH_AUTOTUNE)
+        t_prepare = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, nm, _ = plan.run()
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        info = plan.info()
+        plan.close()
+        solved_b = int(((st == 10) | (st == 20)).sum())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, q in enumerate(P):
+            s_, _, _ = q.solve(1, cap=1)
+            solved_p += s_ in (10, 20)
+            agree += int((s_ in (10, 20)) and (int(st[i]) in (10, 20)) and (s_ == int(st[i])))
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        for q in P:
+            q.close()
+    if world > 1:
+        # whole-job figures: MAX of the times, SUM of the counts
+        tb, solved_b = aggregate_over_ranks(tb, solved_b, world, device)
+        tp, solved_p = aggregate_over_ranks(tp, solved_p, world, device)
+        _, agree = aggregate_over_ranks(0.0, agree, world, device)
+        solved_b, solved_p, agree = int(solved_b), int(solved_p), int(agree)
     return {"workload": f"{a.batch} programs, 4 rules per atom, atoms log-uniform in [200, 20000], "
-                        f"conflict budget {a.batch_conflicts} per program, first answer set",
-            "batched": {"seconds": tb, "solved": solved_b, "solved_per_s": solved_b / tb,
+                        f"conflict budget {a.batch_conflicts} per program, first answer set"
+                        + (f"; {world} ranks, one block of programs each" if world > 1 else ""),
+            "batched": {"seconds": tb, "solved": solved_b, "solved_per_s": solved_b / tb if tb else None,
                         "prepare_seconds": t_prepare, "autotune": info},
-            "plain": {"seconds": tp, "solved": solved_p, "solved_per_s": solved_p / tp},
+            "plain": {"seconds": tp, "solved": solved_p, "solved_per_s": solved_p / tp if tp else None},
             "both_solved_and_agree": agree,
-            "speedup_solved_per_s": (solved_b / tb) / (solved_p / tp) if solved_p else None}
+            "speedup_solved_per_s": (solved_b / tb) / (solved_p / tp) if solved_p and tb and tp else None}
 
 
 def _a11_programs(count, first_index):
