@@ -167,7 +167,9 @@ def run_reference(a, rank, world):
     prog = _program(a)
     per_step = max(a.cpu_seconds / max(a.steps, 1), 1.0)
     import oracle
-    oracle.cdnl(_program_small(), max_models=1)          # warm-up: load and build
+    oracle.cdnl(_program_small(), max_models=1)          # load and build the oracle
+    for _ in range(a.warmup):                            # untimed warm-up steps
+        oracle.cdnl(prog, max_models=1, time_budget_s=per_step)
     checks = props = 0
     t0 = time.perf_counter()
     for _ in range(a.steps):
