@@ -166,6 +166,10 @@ typedef struct {
     int64_t restarts;                           /* restarts (asp_options.restart_conflicts) */
     int64_t conflict_rounds;                    /* rounds that found a conflict; conflicts
                                                    counts every analysed one */
+    int64_t nogood_visits;                      /* nogoods classified by the sweeps (the long
+                                                   and learned ones every sweep, the bucket
+                                                   ones in full sweeps; frontier rounds'
+                                                   nogoods are not counted) */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */
@@ -297,6 +301,21 @@ int asp_debug_last_conflict(asp_prog *p, int64_t *info, int32_t *trail, int64_t 
  * sign 1 = F; returns the length, writes at most cap literals. */
 int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap);
 
+/* Ids of the nogoods learned by the last solve, in the order they were
+ * added (Algorithm 1's learned set: fwd-learning or resolution nogoods,
+ * loop nogoods of the stability step, and the blocking nogoods of the
+ * answer sets found); each id is an offset in the literal store accepted
+ * by asp_debug_nogood.  ids: host buffer of cap entries (may be NULL when
+ * cap is 0).  Returns the number learned (possibly more than cap) or a
+ * negative ASP_E_*. */
+int64_t asp_debug_learned(asp_prog *p, uint32_t *ids, int64_t cap);
+
+/* The compute capability the solve kernel was compiled for
+ * (binary_version, 103 for sm_103a) and its PTX version, as the CUDA
+ * runtime reports them for the current device; either output may be NULL.
+ * Errors: ASP_E_NODEVICE, ASP_E_CUDA. */
+int asp_build_info(int32_t *binary_version, int32_t *ptx_version);
+
 /* ---- learned decision heuristic (not in the paper) ------------------------
  * Decision traces of the last solve, for training: at every Decision step
  * about one applicable rule in eight is sampled, giving one row of
@@ -325,10 +344,11 @@ int asp_mlp_score(const float *weights, const float *features, int64_t n, float 
 
 /* ---- allocation-free propagation ---------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers
- * that cannot allocate device memory where they need propagation -- code
- * running while a stream is being captured into a CUDA graph, real-time
- * loops that must not enter the allocator, or processes whose device memory
- * is reserved up front.  It computes the same closure as
+ * that cannot allocate device memory where they need propagation --
+ * real-time loops that must not enter the allocator (an allocation can
+ * block on the driver or force a synchronising release of cached blocks),
+ * and processes whose device memory is handed out up front by a pool or a
+ * framework that owns all of it.  It computes the same closure as
  * asp_debug_propagate (unit propagation of a root-level partial assignment
  * to fixpoint over the program's nogoods) but keeps all of its working
  * memory in one static device array inside the library: at most 2^20
@@ -342,13 +362,14 @@ int asp_mlp_score(const float *weights, const float *features, int64_t n, float 
  *   d_conflict device int32 output: 1 if a nogood became violated,
  *              -1 on a device-side barrier timeout, else 0
  * The work is enqueued on the program's stream; the call returns without
- * synchronising.  Returns ASP_E_CAPACITY if the program has more than 2^20
- * variables, ASP_E_ARG on null pointers, ASP_E_CUDA on a CUDA error.
- * The first call on a device looks up the device address of the static
- * array (cudaGetSymbolAddress) and the kernel's occupancy; make that first
- * call before any stream capture.  Every call shares the one array: calls
- * that overlap on the GPU (other streams, other host threads) race on it and
- * give wrong results.  Each call clears the counters it needs at zero. */
+ * synchronising.  The device the program was loaded on must be the current
+ * device.  Returns ASP_E_CAPACITY if the program has more than 2^20
+ * variables, ASP_E_ARG on null pointers or when another device is current,
+ * ASP_E_CUDA on a CUDA error.  The first call on a device looks up the
+ * device address of the static array (cudaGetSymbolAddress) and the
+ * kernel's occupancy; make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and give wrong results.  Each call clears the counters it needs at zero. */
 int asp_propagate_noalloc(const asp_prog *p, const int8_t *d_partial, int8_t *d_closure,
                           int32_t *d_conflict);
 

@@ -54,12 +54,13 @@ class Stats(C.Structure):
         "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
         "ns_sweep", "ns_analysis", "ns_decision", "ns_stability", "ns_buckets", "ns_learned",
         "ns_barrier", "view_mode", "batch_view_mode", "ns_slowest_cta", "ns_slowest_sweep",
-        "restarts", "conflict_rounds")]
+        "restarts", "conflict_rounds", "nogood_visits")]
 
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
-           "asp_debug_state", "asp_debug_last_conflict", "asp_debug_nogood", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
+           "asp_debug_state", "asp_debug_last_conflict", "asp_debug_nogood", "asp_debug_learned",
+           "asp_build_info", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
            "asp_mlp_score", "asp_batch_create", "asp_batch_run", "asp_batch_info", "asp_batch_free"]
 
 
@@ -114,6 +115,10 @@ def lib(build_if_missing: bool = True):
         L.asp_debug_last_conflict.restype = C.c_int
         L.asp_debug_nogood.argtypes = [vp, C.c_uint32, vp, i64]
         L.asp_debug_nogood.restype = i64
+        L.asp_debug_learned.argtypes = [vp, vp, i64]
+        L.asp_debug_learned.restype = i64
+        L.asp_build_info.argtypes = [vp, vp]
+        L.asp_build_info.restype = C.c_int
         L.asp_propagate_noalloc.argtypes = [vp, vp, vp, vp]
         L.asp_propagate_noalloc.restype = C.c_int
         L.asp_trace.argtypes = [vp, vp, vp, vp, i64]
@@ -252,6 +257,17 @@ class Program:
         pointers); enqueued on the program's stream.  Returns the ABI code."""
         return lib().asp_propagate_noalloc(self.handle, d_partial, d_closure, d_conflict)
 
+    def learned_ids(self) -> np.ndarray:
+        """Ids of the nogoods the last solve learned, in order (asp_debug_learned)."""
+        n = lib().asp_debug_learned(self.handle, None, 0)
+        if n < 0:
+            raise AspError(n, lib().asp_last_error().decode())
+        ids = np.zeros(max(n, 1), np.uint32)
+        n2 = lib().asp_debug_learned(self.handle, ids.ctypes.data, int(n))
+        if n2 < 0:
+            raise AspError(n2, lib().asp_last_error().decode())
+        return ids[:min(n, n2)].copy()
+
     def trace(self, cap: int = 1 << 16, with_rules: bool = False):
         """Decision trace of the last solve: (features [n, 16], labels [n])
         and, with_rules, the rule index of each row."""
@@ -313,6 +329,13 @@ class Program:
             buf = np.zeros(n, np.int32)
             lib().asp_debug_nogood(self.handle, int(nid), buf.ctypes.data, n)
         return buf[:n].copy()
+
+
+def build_info() -> dict:
+    """asp_build_info: compute capability and PTX version of the solve kernel."""
+    b, p = C.c_int32(), C.c_int32()
+    _check(lib().asp_build_info(C.byref(b), C.byref(p)))
+    return {"binary_version": b.value, "ptx_version": p.value}
 
 
 def solve_batch(programs, max_models_each: int = 1, cap_each: int = 1):

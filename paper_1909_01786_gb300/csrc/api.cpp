@@ -14,6 +14,7 @@
 namespace aspgpu {
 cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t solve_attributes(cudaFuncAttributes *a);
 cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t smem, cudaStream_t st,
                          uint32_t passes);
 int batch_threads(int config);
@@ -69,6 +70,7 @@ namespace aspgpu {
 // for entry points defined in other translation units
 const Dev *internal_dev(const asp_prog *p) { return &p->D; }
 cudaStream_t internal_stream(const asp_prog *p) { return p->stream; }
+int internal_device(const asp_prog *p) { return p->device; }
 int internal_fail(int code, const char *msg);
 }  // namespace aspgpu
 
@@ -430,7 +432,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.n_units = (uint32_t)H.units.size();
     // literal array: buckets (structure-of-arrays) | long CSR | units | learned
     std::vector<uint32_t> lits;
-    unsigned long long bucket_lits = 0;
+    unsigned long long bucket_lits = 0, bucket_ngs = 0;
     for (int L = 2; L <= BUCKET_MAX; L++) {
         const std::vector<uint32_t> &rows = H.bucket_rows[L];
         const uint32_t n = (uint32_t)H.bucket_group[L].size();
@@ -439,6 +441,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
         for (int q = 0; q < L; q++)
             for (uint32_t k = 0; k < n; k++) lits.push_back(rows[(size_t)k * L + q]);
         bucket_lits += (unsigned long long)L * n;
+        bucket_ngs += n;
     }
     std::vector<uint32_t> long_ids(H.long_rel.size());
     const uint32_t long_base = (uint32_t)lits.size();
@@ -448,6 +451,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     for (uint32_t u : H.units) lits.push_back(u | END_BIT);
     D.lits_static = (uint32_t)lits.size();
     D.static_checks = bucket_lits;
+    D.static_nogoods = bucket_ngs;
     int64_t lcap = p->opt.learned_capacity > 0 ? p->opt.learned_capacity
                                                : std::min<int64_t>(std::max<int64_t>(1 << 24, 8 * (int64_t)lits.size()), 1 << 28);
     if ((int64_t)D.lits_static + lcap + 128 >= (int64_t)0xFFFFFF00ll) lcap = (int64_t)0xFFFFFF00ll - D.lits_static - 128;
@@ -667,6 +671,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.view_mode = D.view_mode; o.batch_view_mode = p->D1[0].view_mode;
     o.ns_slowest_cta = (int64_t)s.ns_slowest; o.ns_slowest_sweep = (int64_t)s.ns_slowest_sweep;
     o.restarts = (int64_t)s.restarts; o.conflict_rounds = (int64_t)s.conflict_rounds;
+    o.nogood_visits = (int64_t)s.visits;
 }
 
 extern "C" {
@@ -868,13 +873,12 @@ int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap)
     if (id & BUCKET_ID) {
         const uint32_t L = ((id >> 27) & 15u) + 1u, k = id & 0x7FFFFFFu;
         if (L < 2 || L > (uint32_t)BUCKET_MAX || k >= p->D.bk_n[L]) return fail(ASP_E_ARG, "bad nogood id");
-        for (uint32_t q = 0; q < L; q++) {
-            uint32_t w = 0;
-            cudaError_t e = cudaMemcpy(&w, p->D.lits + p->D.bk_base[L] + (size_t)q * p->D.bk_n[L] + k, 4,
-                                       cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return cuda_fail(e, "nogood");
-            if (q < cap) lits[q] = (int32_t)w;
-        }
+        // literal q sits at bk_base[L] + q * bk_n[L] + k: one strided copy
+        uint32_t w[BUCKET_MAX];
+        cudaError_t e = cudaMemcpy2D(w, 4, p->D.lits + p->D.bk_base[L] + k, (size_t)p->D.bk_n[L] * 4, 4, L,
+                                     cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "nogood");
+        for (uint32_t q = 0; q < L && (int64_t)q < cap; q++) lits[q] = (int32_t)w[q];
         return L;
     }
     if (id >= p->D.lits_cap) return fail(ASP_E_ARG, "bad argument");
@@ -894,6 +898,37 @@ int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap)
     }
     for (int64_t i = 0; i < (int64_t)buf.size() && i < cap; i++) lits[i] = (int32_t)buf[i];
     return (int64_t)buf.size();
+}
+
+int64_t asp_debug_learned(asp_prog *p, uint32_t *ids, int64_t cap)
+{
+    if (!p || cap < 0 || (cap > 0 && !ids)) return fail(ASP_E_ARG, "bad argument");
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    Ctl c[2];
+    e = cudaMemcpy(c, p->D.ctl, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "control");
+    // the count only grows from phase to phase: the larger of the two
+    // control blocks is the last one written
+    const int64_t n = std::min<int64_t>(std::max(c[0].n_learned, c[1].n_learned), p->D.learned_ng_cap);
+    const int64_t k = std::min(n, cap);
+    if (k > 0) {
+        e = cudaMemcpy(ids, p->D.learned_ids, (size_t)k * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "learned ids");
+    }
+    return n;
+}
+
+int asp_build_info(int32_t *binary_version, int32_t *ptx_version)
+{
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(ASP_E_NODEVICE, "no CUDA device");
+    cudaFuncAttributes a;
+    cudaError_t e = solve_attributes(&a);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    if (binary_version) *binary_version = a.binaryVersion;
+    if (ptx_version) *ptx_version = a.ptxVersion;
+    return ASP_OK;
 }
 
 int64_t asp_trace(asp_prog *p, float *features, int32_t *labels, int32_t *rules, int64_t cap)

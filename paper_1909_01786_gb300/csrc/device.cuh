@@ -92,6 +92,9 @@ struct DevStats {
     // sums over phases of the slowest CTA's busy time and sweep time
     unsigned long long ns_slowest, ns_slowest_sweep;
     unsigned long long restarts, conflict_rounds;
+    // nogoods classified by the sweeps (every sweep: the long and learned
+    // nogoods, plus the bucket nogoods when it is a full sweep)
+    unsigned long long visits;
     unsigned int trace_n, pad4;    // trace records written (atomic)
     // the last conflict analysis: conflicting nogood, trail length (claims of
     // the conflict round included), learned nogood id and length, backjump
@@ -134,6 +137,7 @@ struct Dev {
     const uint32_t *vlits;
     long long max_models, models_cap, conflict_budget, time_budget_ns;
     unsigned long long static_checks;    // literals of the buckets (read every sweep)
+    unsigned long long static_nogoods;   // nogoods of the buckets
     uint32_t *lits;                      // buckets | long | units | learned
     const uint32_t *long_ids;
     uint32_t *learned_ids;

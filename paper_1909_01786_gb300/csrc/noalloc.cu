@@ -1,9 +1,10 @@
 // Allocation-free unit propagation (asp_propagate_noalloc).
 //
 // Some callers cannot allocate device memory on the path where they need
-// propagation: code running while a CUDA stream is being captured into a
-// graph, real-time loops that must not touch the allocator, or hosts whose
-// device memory is fully reserved up front.  This entry point computes the
+// propagation: real-time loops that must not enter the allocator (an
+// allocation can block on the driver or trigger a synchronising free of
+// cached blocks), and processes whose device memory is handed out up front
+// by a pool or a framework that owns all of it.  This entry point computes the
 // same closure as asp_debug_propagate, but all of its working memory (the
 // assignment codes, the round counters and the grid barrier) lives in one
 // fixed static device array defined below.  It reads the program's nogood
@@ -207,6 +208,7 @@ int g_noalloc_grid[128];
 
 const Dev *internal_dev(const asp_prog *p);
 cudaStream_t internal_stream(const asp_prog *p);
+int internal_device(const asp_prog *p);
 int internal_fail(int code, const char *msg);
 
 }  // namespace aspgpu
@@ -219,8 +221,13 @@ extern "C" int asp_propagate_noalloc(const asp_prog *p, const int8_t *d_partial,
     const Dev *D = internal_dev(p);
     if (D->nv > NOALLOC_MAX_VARS)
         return internal_fail(ASP_E_CAPACITY, "program has more than 2^20 variables, the static working array's limit");
+    // the program's stream and store belong to the device it was loaded on;
+    // the static array's address is looked up on the current device, so the
+    // two must agree
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return internal_fail(ASP_E_CUDA, "no current device");
+    if (dev != internal_device(p))
+        return internal_fail(ASP_E_ARG, "the current device is not the device the program was loaded on");
     void *scratch = nullptr;
     int grid = 0;
     {
@@ -232,10 +239,15 @@ extern "C" int asp_propagate_noalloc(const asp_prog *p, const int8_t *d_partial,
             if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
                 return internal_fail(ASP_E_CUDA, "cudaGetSymbolAddress of the static working array failed");
             int sms = 0, per_sm = 0;
-            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ASP_E_CUDA;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+                return internal_fail(ASP_E_CUDA, "reading the multiprocessor count failed");
+            // The kernel is compiled for one 768-thread block per SM
+            // (__launch_bounds__(768, 1)), so a grid of one CTA per SM always
+            // fits a cooperative launch; the occupancy query confirms that
+            // at least one block is resident per SM.
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_propagate_kernel, 768, 0) != cudaSuccess ||
                 per_sm < 1)
-                return ASP_E_CUDA;
+                return internal_fail(ASP_E_CUDA, "the propagation kernel cannot be resident on an SM");
             g_noalloc_grid[dev] = sms;
             g_noalloc_ptr[dev] = ptr;
         }

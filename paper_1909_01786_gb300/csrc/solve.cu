@@ -24,6 +24,8 @@ cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block, smem);
 }
 
+cudaError_t solve_attributes(cudaFuncAttributes *a) { return cudaFuncGetAttributes(a, solve_kernel); }
+
 cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st)
 {
     Dev copy = D;

@@ -1743,6 +1743,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 atomicAdd(&D.stats->rounds, 1ull);
                 atomicAdd(&D.stats->props, (unsigned long long)(tend - C.tc));
                 if (sw_full) atomicAdd(&D.stats->checks, D.static_checks);
+                atomicAdd(&D.stats->visits, (sw_full ? D.static_nogoods : 0ull) + D.n_long + C.n_learned);
             }
             break;
         }
@@ -1794,6 +1795,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 atomicAdd(&D.stats->decisions, 1ull);
                 atomicAdd(&D.stats->rounds, 1ull);
                 if (sw_full) atomicAdd(&D.stats->checks, D.static_checks);
+                atomicAdd(&D.stats->visits, (sw_full ? D.static_nogoods : 0ull) + D.n_long + C.n_learned);
                 if ((unsigned long long)L > D.stats->max_level) D.stats->max_level = L;
             }
             break;

@@ -1,9 +1,10 @@
 """asp_propagate_noalloc: propagation for callers that cannot allocate device
-memory (for example while a stream is captured into a CUDA graph).  Its
-working memory is a static device array inside the library, so the test
-checks, through the C ABI, that it gives the same closure as the allocating
-entry point asp_debug_propagate on two calls in a row, and that it refuses a
-program larger than the array.  Collected last so that a failure here never
+memory where they need it (real-time loops that must stay out of the
+allocator, processes whose device memory a pool or framework hands out up
+front).  Its working memory is a static device array inside the library, so
+the test checks, through the C ABI, that it gives the same closure as the
+allocating entry point asp_debug_propagate on two calls in a row, and that it
+refuses a program larger than the array.  Collected last so that a failure here never
 hides another test's result."""
 import ctypes as C
 
