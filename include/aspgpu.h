@@ -60,6 +60,9 @@ extern "C" {
 #define ASP_HEUR_LEARNED_STATIC 3 /* the same score computed once per rule at load, with the
                                      search-state features at their values before the first
                                      decision: a learned static rule order (not in the paper) */
+#define ASP_HEUR_JW 4         /* Jeroslow-Wang (Section 4): sum of 2^-|delta| over the nogoods
+                                 delta holding Fb_r or F head(r), the clauses the decision
+                                 Tb_r satisfies (computed at load) */
 
 /* Shared-memory assignment view of each CTA during the propagate-and-check
  * sweep (Section 4.1; the layout is this implementation's, not the paper's).
@@ -144,6 +147,11 @@ typedef struct {
        shortest of each class of nogood ids mod 3, shorter first; each gives
        a learned nogood and the search backjumps to the lowest target */
     int32_t conflicts_per_round;
+    /* 1: compact completion -- for a rule with an empty positive (negative)
+       body, leave out {Tb_r, Ft_r} ({Tb_r, Fn_r}) and the literal Tt_r (Tn_r)
+       of {Fb_r, Tt_r, Tn_r}; the unit nogood {Ft_r} ({Fn_r}) still sets t_r
+       (n_r) at the root, so the variables and the answer sets are unchanged */
+    int32_t compact;
 } asp_options;
 
 typedef struct {
@@ -309,6 +317,23 @@ int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap);
  * cap is 0).  Returns the number learned (possibly more than cap) or a
  * negative ASP_E_*. */
 int64_t asp_debug_learned(asp_prog *p, uint32_t *ids, int64_t cap);
+
+/* Test-only failure injection at the grid barrier of asp_solve (the
+ * persistent kernel's phase barrier, Algorithm 1's steps run between them):
+ * CTA stall_cta of the solver grid does not arrive at the first phase
+ * barrier -- it waits on a flag that nothing sets -- and every CTA gives up
+ * on a barrier after wait_limit_ms.  The solve then returns ASP_E_DEVICE and
+ * the CUDA context stays usable; the stalled CTA's own wait ends when
+ * another CTA has given up (or after 3 x wait_limit_ms).  stall_cta < 0 and
+ * wait_limit_ms <= 0 restore the defaults (no stall, 20 s).  Applies to
+ * later solves of p.  Errors: ASP_E_ARG. */
+int asp_debug_barrier(asp_prog *p, int32_t stall_cta, int32_t wait_limit_ms);
+
+/* Test-only failure injection on the host: the nth device allocation the
+ * library makes from now on (any program, any thread) fails as if the
+ * allocator had no memory, so the call that needed it returns ASP_E_OOM.
+ * nth = 0 switches it off.  Errors: ASP_E_ARG. */
+int asp_debug_fail_alloc(int64_t nth);
 
 /* The compute capability the solve kernel was compiled for
  * (binary_version, 103 for sm_103a) and its PTX version, as the CUDA

@@ -53,9 +53,9 @@ def _load():
             lib.oracle_least_model_of_reduct.restype = None
             lib.oracle_brute_force.argtypes = [P, C.c_void_p, C.c_int64]
             lib.oracle_brute_force.restype = C.c_int64
-            lib.oracle_completion.argtypes = [P] + [C.c_void_p] * 5
+            lib.oracle_completion.argtypes = [P, C.c_int] + [C.c_void_p] * 5
             lib.oracle_completion.restype = C.c_int
-            lib.oracle_up_closure.argtypes = [P] + [C.c_void_p] * 5
+            lib.oracle_up_closure.argtypes = [P, C.c_int] + [C.c_void_p] * 5
             lib.oracle_up_closure.restype = C.c_int
             lib.oracle_cdnl.argtypes = [P, C.c_int64, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
                                         C.c_void_p, C.c_void_p]
@@ -111,23 +111,27 @@ def brute_force(prog, cap: int = 1 << 16):
     return buf[:n, :prog.n_atoms].copy()
 
 
-def completion(prog):
+def completion(prog, compact: bool = False):
     """The oracle's completion nogoods: (n_vars, off int64[n+1], lits int32)
     with literal +(v+1) = Tv, -(v+1) = Fv and the oracle's interleaved
-    variable layout b_j, t_j, n_j = na+3j, na+3j+1, na+3j+2."""
+    variable layout b_j, t_j, n_j = na+3j, na+3j+1, na+3j+2.  compact: for a
+    rule with an empty positive (negative) body, {Tb_j, Ft_j} ({Tb_j, Fn_j})
+    is left out and Tt_j (Tn_j) is left out of {Fb_j, Tt_j, Tn_j}."""
     b = _Bound(prog)
     lib = _load()
     nn, nl, nv = C.c_int64(), C.c_int64(), C.c_int64()
-    lib.oracle_completion(b.ref, C.byref(nn), C.byref(nl), C.byref(nv), None, None)
+    c = 1 if compact else 0
+    lib.oracle_completion(b.ref, c, C.byref(nn), C.byref(nl), C.byref(nv), None, None)
     off = np.zeros(nn.value + 1, dtype=np.int64)
     lits = np.zeros(max(nl.value, 1), dtype=np.int32)
-    lib.oracle_completion(b.ref, C.byref(nn), C.byref(nl), C.byref(nv), _ptr(off), _ptr(lits))
+    lib.oracle_completion(b.ref, c, C.byref(nn), C.byref(nl), C.byref(nv), _ptr(off), _ptr(lits))
     return nv.value, off, lits[:nl.value]
 
 
-def up_closure(prog, partial):
+def up_closure(prog, partial, compact: bool = False):
     """Unit-propagation closure of a partial assignment over the oracle's
-    variables (1 / -1 / 0).  Returns (conflict, closure, order, reasons)."""
+    variables (1 / -1 / 0) under its completion (compact: the compact
+    variant).  Returns (conflict, closure, order, reasons)."""
     b = _Bound(prog)
     p = np.ascontiguousarray(partial, dtype=np.int8)
     nv = p.shape[0]
@@ -135,7 +139,8 @@ def up_closure(prog, partial):
     order = np.zeros(max(nv, 1), dtype=np.int32)
     reasons = np.zeros(max(nv, 1), dtype=np.int64)
     nd = C.c_int64()
-    conflict = _load().oracle_up_closure(b.ref, _ptr(p), _ptr(clo), _ptr(order), _ptr(reasons), C.byref(nd))
+    conflict = _load().oracle_up_closure(b.ref, 1 if compact else 0, _ptr(p), _ptr(clo), _ptr(order), _ptr(reasons),
+                                         C.byref(nd))
     return bool(conflict), clo, order[:nd.value].copy(), reasons[:nd.value].copy()
 
 

@@ -27,6 +27,9 @@
  *       if it passes O1's check; otherwise a loop nogood is added).
  *   UP  the unit-propagation closure of a partial assignment under the
  *       completion nogoods, by the naive fixpoint of the definition.
+ *   The completion also comes in a compact variant (for empty positive or
+ *   negative bodies, the nogoods that the unit nogood {Ft_r} / {Fn_r}
+ *   settles at the root are left out); O2 uses the full one.
  *
  * Variables: atoms 0..na-1, then for the j-th rule with a head (in rule
  * order) b_j = na+3j, t_j = na+3j+1, n_j = na+3j+2.
@@ -173,8 +176,12 @@ static int64_t rules_with_head(const oprog *P)
 #define FLIT(v) (-((int32_t)(v) + 1))
 
 /* Completion nogoods and constraint nogoods (Section 2).  Body atoms are
- * taken as sets (repeated atoms in one body count once). */
-static void build_completion(const oprog *P, ngdb *d)
+ * taken as sets (repeated atoms in one body count once).
+ * compact != 0: the compact variant.  A rule with no positive body atom has
+ * t_r fixed true by its unit nogood {Ft_r}; then {Tb_r, Ft_r} can never hold
+ * and Tt_r always holds, so that nogood is left out and Tt_r is left out of
+ * {Fb_r, Tt_r, Tn_r}.  Likewise for n_r when the negative body is empty. */
+static void build_completion(const oprog *P, ngdb *d, int compact)
 {
     int32_t na = P->na;
     int32_t buf_cap = 16;
@@ -207,10 +214,22 @@ static void build_completion(const oprog *P, ngdb *d)
         }
         int32_t b = na + 3 * (int32_t)j, t = b + 1, n = b + 2;
         int32_t x[3];
+        int pos_empty = P->pos_off[r + 1] == P->pos_off[r];
+        int neg_empty = P->neg_off[r + 1] == P->neg_off[r];
         /* b_r <-> t_r & n_r */
-        x[0] = FLIT(b); x[1] = TLIT(t); x[2] = TLIT(n); db_add(d, x, 3);
-        x[0] = TLIT(b); x[1] = FLIT(t); db_add(d, x, 2);
-        x[0] = TLIT(b); x[1] = FLIT(n); db_add(d, x, 2);
+        if (!compact) {
+            x[0] = FLIT(b); x[1] = TLIT(t); x[2] = TLIT(n); db_add(d, x, 3);
+            x[0] = TLIT(b); x[1] = FLIT(t); db_add(d, x, 2);
+            x[0] = TLIT(b); x[1] = FLIT(n); db_add(d, x, 2);
+        } else {
+            int32_t m = 0;
+            x[m++] = FLIT(b);
+            if (!pos_empty) x[m++] = TLIT(t);
+            if (!neg_empty) x[m++] = TLIT(n);
+            db_add(d, x, m);
+            if (!pos_empty) { x[0] = TLIT(b); x[1] = FLIT(t); db_add(d, x, 2); }
+            if (!neg_empty) { x[0] = TLIT(b); x[1] = FLIT(n); db_add(d, x, 2); }
+        }
         /* t_r <-> conjunction of body+ */
         int32_t L = 0;
         buf[L++] = FLIT(t);
@@ -261,13 +280,14 @@ static void build_completion(const oprog *P, ngdb *d)
     free(first); free(rl); free(fill); free(cnt); free(seen); free(buf);
 }
 
-/* Export the oracle's own completion: pass NULL buffers to get the sizes. */
-int oracle_completion(const oprog *P, int64_t *n_nogoods, int64_t *n_lits, int64_t *n_vars,
+/* Export the oracle's own completion (compact != 0: the compact variant):
+ * pass NULL buffers to get the sizes. */
+int oracle_completion(const oprog *P, int compact, int64_t *n_nogoods, int64_t *n_lits, int64_t *n_vars,
                       int64_t *off_out, int32_t *lit_out)
 {
     ngdb d;
     db_init(&d);
-    build_completion(P, &d);
+    build_completion(P, &d, compact);
     *n_nogoods = d.n;
     *n_lits = d.nlit;
     *n_vars = P->na + 3 * rules_with_head(P);
@@ -290,12 +310,12 @@ static int lit_opposed(const int8_t *val, int32_t l) { return l > 0 ? val[l - 1]
  * that were added) and each derived literal's reason nogood index.
  * Returns 1 on conflict (closure then holds the state when it was found),
  * 0 otherwise. */
-int oracle_up_closure(const oprog *P, const int8_t *partial, int8_t *closure,
+int oracle_up_closure(const oprog *P, int compact, const int8_t *partial, int8_t *closure,
                       int32_t *order, int64_t *reasons, int64_t *n_derived)
 {
     ngdb d;
     db_init(&d);
-    build_completion(P, &d);
+    build_completion(P, &d, compact);
     int64_t nv = P->na + 3 * rules_with_head(P);
     memcpy(closure, partial, (size_t)nv);
     int64_t nd = 0;
@@ -542,7 +562,7 @@ int oracle_cdnl(const oprog *P, int64_t max_models, int64_t conflict_budget, dou
     S.rule_of = (int32_t *)malloc(sizeof(int32_t) * ((size_t)S.nrr + 1));
     for (int32_t r = 0, j = 0; r < P->nr; r++) if (P->head[r] >= 0) S.rule_of[j++] = r;
     db_init(&S.db);
-    build_completion(P, &S.db);
+    build_completion(P, &S.db, 0);
     S.n_static = S.db.n;
     size_t nv = (size_t)S.nv + 1;
     S.occ = (int64_t **)calloc(nv, sizeof(int64_t *));

@@ -17,7 +17,7 @@ from . import build as _build
 
 ASP_OK, ASP_E_CAPACITY = 0, -5
 MLP_FEATURES, MLP_PARAMS = 16, 1153
-HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED = 0, 1, 2
+HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED, HEUR_LEARNED_STATIC, HEUR_JW = 0, 1, 2, 3, 4
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 VIEW_AUTO, VIEW_PLAIN, VIEW_PACKED, VIEW_BYTES = 0, 1, 2, 3
 LEARN_FWD, LEARN_RES = 0, 1
@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("mlp_weights", C.c_void_p), ("trace_capacity", C.c_int64),
                 ("view_mode", C.c_int32), ("frontier", C.c_int32), ("learning", C.c_int32),
                 ("backjump", C.c_int32), ("restart_conflicts", C.c_int32),
-                ("conflicts_per_round", C.c_int32)]
+                ("conflicts_per_round", C.c_int32), ("compact", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -60,7 +60,7 @@ class Stats(C.Structure):
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
            "asp_debug_state", "asp_debug_last_conflict", "asp_debug_nogood", "asp_debug_learned",
-           "asp_build_info", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
+           "asp_build_info", "asp_debug_barrier", "asp_debug_fail_alloc", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
            "asp_mlp_score", "asp_batch_create", "asp_batch_run", "asp_batch_info", "asp_batch_free"]
 
 
@@ -119,6 +119,10 @@ def lib(build_if_missing: bool = True):
         L.asp_debug_learned.restype = i64
         L.asp_build_info.argtypes = [vp, vp]
         L.asp_build_info.restype = C.c_int
+        L.asp_debug_barrier.argtypes = [vp, i32, i32]
+        L.asp_debug_barrier.restype = C.c_int
+        L.asp_debug_fail_alloc.argtypes = [i64]
+        L.asp_debug_fail_alloc.restype = C.c_int
         L.asp_propagate_noalloc.argtypes = [vp, vp, vp, vp]
         L.asp_propagate_noalloc.restype = C.c_int
         L.asp_trace.argtypes = [vp, vp, vp, vp, i64]
@@ -170,7 +174,7 @@ class Program:
     def __init__(self, prog, *, heuristic=0, deps_levels=0, conflict_budget=0, time_budget_ms=120_000,
                  learned_capacity=0, grid_ctas=0, block_threads=0, stream=None, torch_memory=True,
                  mlp_weights=None, trace_capacity=0, view_mode=0, frontier=False, learning=LEARN_FWD,
-                 backjump=BACKJUMP_H_MINUS_1, restart_conflicts=0, conflicts_per_round=1):
+                 backjump=BACKJUMP_H_MINUS_1, restart_conflicts=0, conflicts_per_round=1, compact=False):
         L = lib()
         self.n_atoms = int(prog.n_atoms)
         self._keep = []
@@ -188,6 +192,7 @@ class Program:
         opt.backjump = int(backjump)
         opt.restart_conflicts = int(restart_conflicts)
         opt.conflicts_per_round = int(conflicts_per_round)
+        opt.compact = 1 if compact else 0
         opt.heuristic, opt.deps_levels = heuristic, deps_levels
         opt.conflict_budget, opt.time_budget_ms = conflict_budget, time_budget_ms
         opt.learned_capacity, opt.grid_ctas, opt.block_threads = learned_capacity, grid_ctas, block_threads

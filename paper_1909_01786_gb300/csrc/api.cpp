@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -74,10 +75,14 @@ int internal_device(const asp_prog *p) { return p->device; }
 int internal_fail(int code, const char *msg);
 }  // namespace aspgpu
 
+// test-only: the n-th device allocation from now on fails (0 = none)
+static std::atomic<int64_t> g_alloc_fail_in{0};
+
 static void *dalloc(asp_prog *p, size_t bytes)
 {
     bytes = std::max<size_t>(bytes, 16);
     void *ptr = nullptr;
+    if (g_alloc_fail_in.load() > 0 && g_alloc_fail_in.fetch_sub(1) == 1) return nullptr;
     if (p->opt.dev_alloc) {
         ptr = p->opt.dev_alloc(bytes, p->opt.alloc_ctx);
     } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
@@ -413,7 +418,8 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     }
     HostStore H;
     std::string err;
-    int rc = build_store(n_atoms, n_rules, head, pos_off, pos, neg_off, neg, H, err);
+    int rc = build_store(n_atoms, n_rules, head, pos_off, pos, neg_off, neg, H, err,
+                         opt && opt->compact != 0);
     if (rc != ASP_OK) return fail(rc, err);
 
     asp_prog *p = new asp_prog();
@@ -464,7 +470,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.WW = WW;
     D.Wlevels = WW * 64u;
     D.heuristic = (uint32_t)std::max(0, p->opt.heuristic);
-    if (D.heuristic > 3) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
+    if (D.heuristic > 4) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
     if (p->opt.learning < 0 || p->opt.learning > 1) { delete p; return fail(ASP_E_ARG, "unknown learning"); }
     D.learning = (uint32_t)p->opt.learning;
     if (p->opt.backjump < 0 || p->opt.backjump > 1 || p->opt.restart_conflicts < 0) {
@@ -478,6 +484,8 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
         return fail(ASP_E_ARG, "conflicts_per_round must be 0..4");
     }
     D.conf_per_round = (uint32_t)std::max(1, p->opt.conflicts_per_round);
+    D.stall_cta = 0xFFFFFFFFu;
+    D.barrier_ns = 20000000000ull;
     p->n_nogoods = H.n_nogoods;
     p->n_literals = H.n_literals;
     p->n_units = (int64_t)H.units.size();
@@ -500,9 +508,9 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     if (rc == ASP_OK) D.rpos = upload(p, H.rpos, rc);
     if (rc == ASP_OK) D.rneg_off = upload(p, H.rneg_off, rc);
     if (rc == ASP_OK) D.rneg = upload(p, H.rneg, rc);
-    if (rc == ASP_OK) D.score = upload(p, H.score, rc);
+    if (rc == ASP_OK) D.score = upload(p, D.heuristic == 4 ? H.score_jw : H.score, rc);
     if (rc == ASP_OK) D.rfeat = upload(p, H.rfeat, rc);
-    if (rc == ASP_OK && D.heuristic >= 2) {
+    if (rc == ASP_OK && (D.heuristic == 2 || D.heuristic == 3)) {
         if (!p->opt.mlp_weights) rc = fail(ASP_E_ARG, "learned heuristic without mlp_weights");
         else {
             // bf16 by round-to-nearest-even of the float bits
@@ -917,6 +925,22 @@ int64_t asp_debug_learned(asp_prog *p, uint32_t *ids, int64_t cap)
         if (e != cudaSuccess) return cuda_fail(e, "learned ids");
     }
     return n;
+}
+
+int asp_debug_barrier(asp_prog *p, int32_t stall_cta, int32_t wait_limit_ms)
+{
+    if (!p) return fail(ASP_E_ARG, "bad argument");
+    if (stall_cta >= p->grid) return fail(ASP_E_ARG, "stall_cta is not a CTA of the solver grid");
+    p->D.stall_cta = stall_cta < 0 ? 0xFFFFFFFFu : (uint32_t)stall_cta;
+    p->D.barrier_ns = wait_limit_ms > 0 ? (unsigned long long)wait_limit_ms * 1000000ull : 20000000000ull;
+    return ASP_OK;
+}
+
+int asp_debug_fail_alloc(int64_t nth)
+{
+    if (nth < 0) return fail(ASP_E_ARG, "bad argument");
+    g_alloc_fail_in.store(nth);
+    return ASP_OK;
 }
 
 int asp_build_info(int32_t *binary_version, int32_t *ptx_version)

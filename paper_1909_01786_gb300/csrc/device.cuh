@@ -104,8 +104,9 @@ struct DevStats {
 
 // Grid barrier: arrivals counted since the solve began (barrier g is
 // complete once count >= (g + 1) * CTAs); err is set by a CTA that gave up
-// waiting.
-struct Barrier { unsigned long long count; unsigned int err, pad; };
+// waiting; stall is a flag that nothing sets (the test-only stalled CTA
+// waits on it).
+struct Barrier { unsigned long long count; unsigned int err, stall; };
 
 struct Dev {
     uint32_t na, J, nv, asg_words;
@@ -121,7 +122,11 @@ struct Dev {
     uint32_t backjump, restart_unit;
     // conflicts analysed per conflicting round (1..4): the shortest, then
     // the shortest of each class id % 3; the lowest target wins
-    uint32_t conf_per_round, pad2;
+    uint32_t conf_per_round;
+    // test-only failure injection: this CTA does not arrive at the first
+    // phase barrier (0xFFFFFFFF = none); it waits, bounded, on a flag that
+    // nothing sets until another CTA gives up on the barrier
+    uint32_t stall_cta;
     // static partition of the buckets over the CTAs by groups (atoms and
     // their rules; constraints): CTA g owns nogoods [cta_boff[L*(G+1)+g],
     // cta_boff[L*(G+1)+g+1]) of bucket L, and keeps in shared memory the
@@ -138,6 +143,7 @@ struct Dev {
     long long max_models, models_cap, conflict_budget, time_budget_ns;
     unsigned long long static_checks;    // literals of the buckets (read every sweep)
     unsigned long long static_nogoods;   // nogoods of the buckets
+    unsigned long long barrier_ns;       // grid barrier: give up after this wait
     uint32_t *lits;                      // buckets | long | units | learned
     const uint32_t *long_ids;
     uint32_t *learned_ids;

@@ -68,10 +68,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 }
 
 // Grid barrier with a bounded wait: returns false (and sets the sticky error
-// flag) if the other CTAs do not arrive within ~20 s, or if another CTA gave
-// up.  One atomic per CTA on a counter that is never reset: the barrier an
-// arrival belongs to is its count divided by the number of CTAs.
-__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks)
+// flag) if the other CTAs do not arrive within limit_ns (20 s unless a test
+// shortens it), or if another CTA gave up.  One atomic per CTA on a counter
+// that is never reset: the barrier an arrival belongs to is its count
+// divided by the number of CTAs.
+__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks, unsigned long long limit_ns)
 {
     __shared__ int s_ok;
     cta_sync();
@@ -88,7 +89,7 @@ __device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks)
                         if (ld_acquire_u32(&b->err)) { ok = 0; break; }
                         const unsigned long long now = globaltimer_ns();
                         if (t0 == 0) t0 = now;
-                        else if (now - t0 > 20000000000ull) {
+                        else if (now - t0 > limit_ns) {
                             atomicExch(&b->err, 1u);
                             ok = 0;
                             break;
@@ -1533,7 +1534,22 @@ __device__ __forceinline__ bool group_sync(const Dev &D)
         cta_sync();
         return true;
     }
-    return grid_sync(D.bar, gridDim.x);
+    return grid_sync(D.bar, gridDim.x, D.barrier_ns);
+}
+
+// Test-only failure injection: CTA D.stall_cta (thread 0) waits on a flag
+// that nothing sets, so it does not reach the first phase barrier in time.
+// The wait ends when another CTA has given up on that barrier (its error
+// flag) or after three times the barrier's limit, whichever comes first.
+__device__ __forceinline__ void injected_stall(const Dev &D)
+{
+    if (blockIdx.x != D.stall_cta || threadIdx.x != 0) return;
+    const unsigned long long t0 = globaltimer_ns();
+    while (ld_acquire_u32(&D.bar->stall) == 0u) {
+        if (ld_acquire_u32(&D.bar->err)) break;
+        if (globaltimer_ns() - t0 > 3ull * D.barrier_ns) break;
+        __nanosleep(1000);
+    }
 }
 
 // Algorithm 1 on the device.  rank/size: thread index and thread count of
@@ -2021,6 +2037,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         }
         const unsigned long long tb0 = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
         if (threadIdx.x == 0) atomicMax(&acc->tbusy, tb0 - t_cta0);
+        if (!BATCH && k == 0 && D.stall_cta != 0xFFFFFFFFu) injected_stall(D);
         if (!group_sync<BATCH>(D)) break;
         if (threadIdx.x == 0) t_cta0 = globaltimer_ns();
         if (leader) ns_bar += t_cta0 - tb0;

@@ -50,7 +50,7 @@ struct Packer {
 int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
                 const int64_t *pos_off, const int32_t *pos,
                 const int64_t *neg_off, const int32_t *neg,
-                HostStore &S, std::string &err)
+                HostStore &S, std::string &err, bool compact)
 {
     if (n_atoms < 0 || n_rules < 0) { err = "negative size"; return ASP_E_ARG; }
     if (n_rules > 0 && (!head || !pos_off || !neg_off)) { err = "null rule array"; return ASP_E_ARG; }
@@ -118,10 +118,19 @@ int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     auto rule_nogoods = [&](uint32_t j) {
         uint32_t b = bvar(j), t = tvar(j), n = nvar(j);
         uint32_t x[3];
-        // b_r <-> t_r & n_r : {Fb,Tt,Tn} {Tb,Ft} {Tb,Fn}
-        x[0] = mk_lit(b, true); x[1] = mk_lit(t, false); x[2] = mk_lit(n, false); pk.add(x, 3);
-        x[0] = mk_lit(b, false); x[1] = mk_lit(t, true); pk.add(x, 2);
-        x[0] = mk_lit(b, false); x[1] = mk_lit(n, true); pk.add(x, 2);
+        // b_r <-> t_r & n_r : {Fb,Tt,Tn} {Tb,Ft} {Tb,Fn}.  Compact: with an
+        // empty B+ (B-) the unit nogood {Ft} ({Fn}) below makes t_r (n_r)
+        // true at the root, so {Tb,Ft} ({Tb,Fn}) can never be violated and
+        // Tt (Tn) always holds in {Fb,Tt,Tn}.
+        const bool t_const = compact && S.rpos_off[j + 1] == S.rpos_off[j];
+        const bool n_const = compact && S.rneg_off[j + 1] == S.rneg_off[j];
+        int m = 0;
+        x[m++] = mk_lit(b, true);
+        if (!t_const) x[m++] = mk_lit(t, false);
+        if (!n_const) x[m++] = mk_lit(n, false);
+        pk.add(x, m);
+        if (!t_const) { x[0] = mk_lit(b, false); x[1] = mk_lit(t, true); pk.add(x, 2); }
+        if (!n_const) { x[0] = mk_lit(b, false); x[1] = mk_lit(n, true); pk.add(x, 2); }
         // t_r <-> body+ : {Tt,Fp} per p, {Ft} u {Tp}
         buf.assign(1, mk_lit(t, true));
         for (uint32_t k = S.rpos_off[j]; k < S.rpos_off[j + 1]; k++) {
@@ -170,6 +179,36 @@ int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     for (uint32_t u : S.units) count(u);
     S.score.resize(J);
     for (uint32_t j = 0; j < J; j++) S.score[j] = occ[S.rule_head[j]];
+
+    // Jeroslow-Wang score (Section 4 names it among the decision
+    // heuristics): a nogood delta is the clause "not all of delta", which a
+    // literal l satisfies when its complement is in delta, weighted 2^-|delta|.
+    // Deciding Tb_r makes b_r true and then head(r) true, so the score of rule
+    // r is the sum of 2^-|delta| over the nogoods holding Fb_r or F head(r),
+    // in fixed point (x 2^16, saturating).
+    std::vector<uint64_t> jw_f((size_t)nv + 1, 0);     // per variable: sum over nogoods with its F literal
+    auto jw_add = [&](const uint32_t *l, size_t len) {
+        const uint64_t w = len < 17 ? (1ull << (16 - len)) : 0ull;
+        for (size_t q = 0; q < len; q++) {
+            const uint32_t lit = l[q] & ~END_BIT;
+            if (lit & 1u) jw_f[lit >> 1] += w;
+        }
+    };
+    for (int L = 2; L <= BUCKET_MAX; L++) {
+        const std::vector<uint32_t> &rows = S.bucket_rows[L];
+        for (size_t t = 0; t + (size_t)L <= rows.size(); t += (size_t)L) jw_add(rows.data() + t, (size_t)L);
+    }
+    for (size_t i = 0; i < S.long_rel.size(); i++) {
+        const size_t s0 = S.long_rel[i];
+        const size_t s1 = i + 1 < S.long_rel.size() ? S.long_rel[i + 1] : S.long_lits.size();
+        jw_add(S.long_lits.data() + s0, s1 - s0);
+    }
+    for (uint32_t u : S.units) jw_add(&u, 1);
+    S.score_jw.resize(J);
+    for (uint32_t j = 0; j < J; j++) {
+        const uint64_t sc = jw_f[bvar(j)] + jw_f[(uint32_t)S.rule_head[j]];
+        S.score_jw[j] = (uint32_t)std::min<uint64_t>(sc, 0x7FFFFFFFull);
+    }
 
     // static features of each rule (inputs of the learned heuristic):
     // log1p occurrences of the head, |B+|, |B-|, log1p |rules(head)|,

@@ -47,16 +47,20 @@ struct HostStore {
     std::vector<int32_t> rule_head;                  // [n_headed]
     std::vector<uint32_t> rpos_off, rpos, rneg_off, rneg;
     std::vector<uint32_t> score;                     // static decision score per headed rule
+    std::vector<uint32_t> score_jw;                  // Jeroslow-Wang score per headed rule (x 2^16)
     std::vector<float> rfeat;                        // [n_headed][8] static features of each rule
 };
 
 // static features per rule for the learned decision heuristic
 constexpr int RULE_STATIC_FEATURES = 8;
 
-// Returns 0 or a negative ASP_E_* code with a message in err.
+// Returns 0 or a negative ASP_E_* code with a message in err.  compact:
+// for a rule with an empty positive (negative) body, leave out the nogoods
+// that the unit nogood {Ft_r} ({Fn_r}) satisfies at the root and drop the
+// literal Tt_r (Tn_r) from {Fb_r, Tt_r, Tn_r}.
 int build_store(int32_t n_atoms, int32_t n_rules, const int32_t *head,
                 const int64_t *pos_off, const int32_t *pos,
                 const int64_t *neg_off, const int32_t *neg,
-                HostStore &out, std::string &err);
+                HostStore &out, std::string &err, bool compact = false);
 
 }  // namespace aspgpu
