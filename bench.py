@@ -55,12 +55,20 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=256,
                     help="programs of the batched workload (config-4 family); 0 = skip")
-    ap.add_argument("--batch-conflicts", type=int, default=100, help="per-program conflict budget")
+    ap.add_argument("--batch-conflicts", type=int, default=2000, help="per-program conflict budget (batched leg)")
+    ap.add_argument("--learned-conflicts", type=int, default=100,
+                    help="per-program conflict budget of the learned-heuristic and search-option legs")
     ap.add_argument("--learned", type=int, default=256,
                     help="held-out programs for the learned-heuristic comparison; 0 = skip")
     ap.add_argument("--learned-train", type=int, default=1024, help="training programs (traces)")
     ap.add_argument("--no-learning-compare", action="store_true",
                     help="skip the fwd-learning vs first-UIP resolution comparison")
+    ap.add_argument("--big-atoms", type=int, default=400_000,
+                    help="atoms of the store-larger-than-L2 program (4 rules per atom); 0 = skip that leg")
+    ap.add_argument("--big-conflicts", type=int, default=40, help="conflict budget of the in-solver leg on it")
+    ap.add_argument("--tiny", type=int, default=1000, help="tiny programs enumerated (config-1 family); 0 = skip")
+    ap.add_argument("--batch-rules-per-atom", type=int, default=2,
+                    help="rules per atom of the batched workload (2: the family decides within the budget)")
     ap.add_argument("--sweep-only", type=int, default=0,
                     help="profiling aid: load the program and run this many standalone sweeps")
     return ap.parse_args()
@@ -240,7 +248,7 @@ def run_ours(a, rank, world, local_rank):
         step()
     torch.cuda.synchronize(dev)
 
-    totals = dict(literal_checks=0, propagations=0, decisions=0, conflicts=0, rounds=0,
+    totals = dict(literal_checks=0, nogood_visits=0, propagations=0, decisions=0, conflicts=0, rounds=0,
                   max_level=0, learned=0, learned_literals=0,
                   ns_total=0, ns_sweep=0, ns_analysis=0, ns_decision=0, ns_stability=0,
                   ns_buckets=0, ns_learned=0, ns_barrier=0, ns_slowest_cta=0, ns_slowest_sweep=0)
@@ -264,24 +272,37 @@ def run_ours(a, rank, world, local_rank):
     ms, checks_all = aggregate_over_ranks(ms, checks, world, dev)
     value = checks_all / (ms / 1e3)
 
-    # dominant kernel: the persistent solve kernel (one launch per step)
+    # dominant kernel: the persistent solve kernel (one launch per step).
+    # Algorithmic bytes: 4 B per literal read and classified plus 4 B per
+    # nogood visited (the literal word and the CSR offset a store with
+    # offsets would read), over the nogoods the sweeps scanned.
     peaks = _peaks()
     peak = peaks.get("hbm_gbs")
-    achieved = 4.0 * checks / (ms / 1e3) / 1e9          # algorithmic bytes: 4 B per literal check
+    visits = totals["nogood_visits"]
+    alg_bytes = 4.0 * checks + 4.0 * visits
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    achieved_4b = 4.0 * checks / (ms / 1e3) / 1e9
     sha = _src_sha()
     traffic = _traffic(sha, checks / max(len(ev), 1), a.atoms, a.rules)
+    store_mb = P.stats()['store_bytes'] / 1e6
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if peak else None,
                 "traffic": traffic, "kernel": "solve_kernel",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peak else None,
-                "note": f"store of {P.stats()['store_bytes'] / 1e6:.0f} MB; achieved counts 4 B per literal check; "
-                        "traffic = DRAM bytes per literal check from an ncu capture of a 20-conflict launch "
-                        "of this workload x this launch's checks"}
+                "bytes_per_launch": alg_bytes / max(len(ev), 1),
+                "achieved_4B_per_check": achieved_4b,
+                "frac_4B_per_check": (achieved_4b / peak) if peak else None,
+                "regime": (f"store of {store_mb:.0f} MB stays in L2 (126 MB): the sweep is bound by L2 and "
+                           "shared-memory latency, not HBM; the HBM-bound figure is the big_store leg"
+                           if store_mb < 100 else f"store of {store_mb:.0f} MB streams from HBM"),
+                "note": "achieved = (4 B x literal checks + 4 B x nogood visits) / kernel time (Sigma(4 len + 4) "
+                        "over scanned nogoods); traffic = DRAM bytes per literal check from an ncu capture "
+                        "of a 20-conflict launch of this workload x this launch's checks"}
 
     # sweep kernel alone: one launch loads the shared-memory views once and
     # makes K passes; per-pass time = (t(K+1) - t(1)) / K
     st = P.stats()
-    sweep_bytes = 4 * (st["n_literals"] - st["n_unit_nogoods"])
+    sweep_bytes = 4 * (st["n_literals"] - st["n_unit_nogoods"]) + 4 * (st["n_nogoods"] - st["n_unit_nogoods"])
 
     def timed(passes, reps=5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -297,6 +318,7 @@ def run_ours(a, rank, world, local_rank):
     t1, tk = timed(1), timed(K + 1)
     per_pass = (tk - t1) / K
     sweep = {"ms_per_pass": per_pass, "ms_view_load_and_one_pass": t1, "bytes_per_pass": sweep_bytes,
+             "bytes_rule": "Sigma(4 len + 4) over the non-unit nogoods",
              "achieved_gbs": sweep_bytes / (per_pass / 1e3) / 1e9,
              "frac_of_hbm": (sweep_bytes / (per_pass / 1e3) / 1e9) / peak if peak else None,
              "note": (f"store of {st['store_bytes'] / 1e6:.0f} MB "
@@ -310,7 +332,7 @@ def run_ours(a, rank, world, local_rank):
         e2e = None
         if not a.no_e2e:
             e2e_checks, t_e2e, h2d = 0, 0.0, 0
-            n_e2e = max(1, min(a.steps, 2))
+            n_e2e = max(1, a.steps)
             for _ in range(n_e2e):
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
@@ -324,8 +346,11 @@ def run_ours(a, rank, world, local_rank):
             d2h = words * 8 + 32
             e2e = {"value": e2e_checks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
+        big = _big_store(a, aspgpu, torch, dev, peak) if a.big_atoms > 0 else None
+        tiny = _tiny(a, aspgpu, torch) if a.tiny > 0 else None
         learned = _learned(a, aspgpu, torch) if a.learned > 0 else None
         learning = None if a.no_learning_compare else _learning(a, aspgpu, prog)
+        frontiers = _frontiers(a, aspgpu, prog)
         options = None if a.no_learning_compare or a.learned <= 0 else _search_options(a, aspgpu, torch)
         cpu = None if a.no_cpu else _cpu_baseline(prog, a.cpu_seconds)
         tsec = ms / 1e3
@@ -340,8 +365,10 @@ def run_ours(a, rank, world, local_rank):
                        "view": {1: "plain 2-bit", 2: "packed 2-bit", 3: "bytes"}.get(st["view_mode"]),
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": a.steps,
-            "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "batched": batched,
+            "roofline": roofline, "sweep_kernel": sweep, "cpu_baseline": cpu, "big_store": big,
+            "tiny_programs": tiny, "batched": batched,
             "learned_heuristic": learned, "learning_compare": learning, "search_options": options,
+            "frontier_compare": frontiers,
             "clocks": clk.summary(),
             "search": {"statuses": statuses, "decisions_per_s": totals["decisions"] / tsec,
                        "propagations_per_s": totals["propagations"] / tsec,
@@ -354,6 +381,8 @@ def run_ours(a, rank, world, local_rank):
                                                            "ns_slowest_sweep")}},
             "solver_src_sha": sha,
         }
+        out["work_vs_oracle"] = _work_ratios(out)
+        out["summary"] = _summary(out)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -391,6 +420,35 @@ def _learning(a, aspgpu, prog):
     return out
 
 
+def _frontiers(a, aspgpu, prog):
+    """The same search (same program, budget and heuristic) under each
+    propagation-round mode: full sweeps, the nogood frontier (occurrence
+    lists), and the unit frontier (dirty bucket units).  Device time, rates,
+    rounds per decision, and literals and nogoods checked per round."""
+    out = {}
+    for name, fr in (("full", aspgpu.FRONTIER_FULL), ("nogoods", aspgpu.FRONTIER_NOGOODS),
+                     ("units", aspgpu.FRONTIER_UNITS)):
+        P = aspgpu.Program(prog, frontier=fr, conflict_budget=a.conflicts, time_budget_ms=60_000, view_mode=a.view)
+        P.solve(1, cap=1)                          # warm-up solve
+        status, _, _ = P.solve(1, cap=1)
+        s = P.stats()
+        sec = max(s["ns_total"], 1) / 1e9
+        rounds = max(s["rounds"], 1)
+        out[name] = {"status": int(status), "device_s": sec, "conflicts": s["conflicts"],
+                     "decisions_per_s": s["decisions"] / sec, "propagations_per_s": s["propagations"] / sec,
+                     "conflicts_per_s": s["conflicts"] / sec, "rounds_per_s": s["rounds"] / sec,
+                     "rounds_per_decision": s["rounds"] / max(s["decisions"], 1),
+                     "us_per_round": s["ns_total"] / rounds / 1e3,
+                     "literal_checks_per_round": s["literal_checks"] / rounds,
+                     "nogood_visits_per_round": s["nogood_visits"] / rounds,
+                     "literal_checks_per_s": s["literal_checks"] / sec}
+        P.close()
+    full = out["full"]["decisions_per_s"]
+    for v in out.values():
+        v["decisions_per_s_vs_full"] = v["decisions_per_s"] / full if full else None
+    return out
+
+
 def shard_bounds(count, rank, world):
     """Rank `rank`'s contiguous block [lo, hi) of `count` independent programs
     (sizes are drawn i.i.d., so blocks are alike); blocks differ by at most one."""
@@ -399,21 +457,46 @@ def shard_bounds(count, rank, world):
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def _oracle_first(args):
+    prog, budget_s = args
+    import oracle
+    t = time.perf_counter()
+    st, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=budget_s)
+    return st, time.perf_counter() - t
+
+
+def _oracle_pool(progs, budget_s):
+    """The oracle's CDNL, one program per host core (spawned workers)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_first, [(p, budget_s) for p in progs], chunksize=4)
+    return [r[0] for r in res], [r[1] for r in res], time.perf_counter() - t0, cores
+
+
 def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
-    """Batched vs plain on the same programs: 4 rules per atom, atom counts
-    log-uniform in [200, 20000], seeds (4 << 32) | i; per-program conflict
-    budget.  solved = SAT or UNSAT within the budget.  Under N ranks each
-    rank solves its own block of the programs (no exchange of data); the
-    job reports all ranks' solved programs over the slowest rank's time."""
+    """Batched vs plain on the same programs: atom counts log-uniform in
+    [200, 20000], rules = k x atoms (k = --batch-rules-per-atom; at 2 the
+    family decides within the budget, at 4 almost nothing does), seeds
+    (4 << 32) | i; per-program conflict budget.  solved = SAT or UNSAT within
+    the budget.  The oracle's CDNL runs beside them on every host core, and
+    its statuses are compared wherever both decide.  Under N ranks each rank
+    solves its own block of the programs (no exchange of data); the job
+    reports all ranks' solved programs over the slowest rank's time."""
+    import numpy as np
     from synth.programs import batch_programs
     lo, hi = shard_bounds(a.batch, rank, world)
-    progs = batch_programs(hi - lo, rules_per_atom=4, config_id=4, first_index=lo) if hi > lo else []
+    rpa = a.batch_rules_per_atom
+    progs = batch_programs(hi - lo, rules_per_atom=rpa, config_id=4, first_index=lo) if hi > lo else []
     kw = dict(conflict_budget=a.batch_conflicts, time_budget_ms=20_000, deps_levels=1024,
               learned_capacity=1 << 20)
     P = [aspgpu.Program(p, **kw) for p in progs]
     solved_b = solved_p = agree = 0
     tb = tp = t_prepare = 0.0
     info = None
+    st = np.zeros(0, np.int32)
+    plain_ms = []
     if P:
         # autotuned configuration, launch captured in a CUDA graph; the timed
         # region replays it once
@@ -431,27 +514,173 @@ def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i, q in enumerate(P):
+            t1 = time.perf_counter()
             s_, _, _ = q.solve(1, cap=1)
+            plain_ms.append((time.perf_counter() - t1) * 1e3)
             solved_p += s_ in (10, 20)
             agree += int((s_ in (10, 20)) and (int(st[i]) in (10, 20)) and (s_ == int(st[i])))
         torch.cuda.synchronize()
         tp = time.perf_counter() - t0
         for q in P:
             q.close()
+    oracle_part = None
+    if rank == 0 and progs:
+        ost, osec, owall, cores = _oracle_pool(progs, 2.0)
+        ost = np.array(ost)
+        od = (ost == 10) | (ost == 20)
+        gd = (st == 10) | (st == 20)
+        both = od & gd
+        oracle_part = {"solved": int(od.sum()), "seconds": owall, "cores": cores,
+                       "solved_per_s": int(od.sum()) / owall if owall else None,
+                       "budget": "2 s of CPU per program", "decided_by_both": int(both.sum()),
+                       "status_mismatches": int((ost[both] != st[both]).sum())}
     if world > 1:
         # whole-job figures: MAX of the times, SUM of the counts
         tb, solved_b = aggregate_over_ranks(tb, solved_b, world, device)
         tp, solved_p = aggregate_over_ranks(tp, solved_p, world, device)
         _, agree = aggregate_over_ranks(0.0, agree, world, device)
         solved_b, solved_p, agree = int(solved_b), int(solved_p), int(agree)
-    return {"workload": f"{a.batch} programs, 4 rules per atom, atoms log-uniform in [200, 20000], "
+    pct = (lambda q: float(np.percentile(plain_ms, q)) if plain_ms else None)
+    return {"workload": f"{a.batch} programs, {rpa} rules per atom, atoms log-uniform in [200, 20000], "
                         f"conflict budget {a.batch_conflicts} per program, first answer set"
                         + (f"; {world} ranks, one block of programs each" if world > 1 else ""),
             "batched": {"seconds": tb, "solved": solved_b, "solved_per_s": solved_b / tb if tb else None,
                         "prepare_seconds": t_prepare, "autotune": info},
-            "plain": {"seconds": tp, "solved": solved_p, "solved_per_s": solved_p / tp if tp else None},
+            "plain": {"seconds": tp, "solved": solved_p, "solved_per_s": solved_p / tp if tp else None,
+                      "ms_per_program_p50_p90_max": [pct(50), pct(90), max(plain_ms) if plain_ms else None]},
+            "oracle_all_cores": oracle_part,
             "both_solved_and_agree": agree,
             "speedup_solved_per_s": (solved_b / tb) / (solved_p / tp) if solved_p and tb and tp else None}
+
+
+def _big_store(a, aspgpu, torch, dev, peak):
+    """The store larger than L2: a random program of --big-atoms atoms and 4
+    rules per atom (seed (2 << 32) | 7).  The standalone sweep per pass
+    (HBM-bound: the store streams every pass) and the solve kernel with a
+    small conflict budget, both with algorithmic bytes Sigma(4 len + 4)."""
+    from synth.programs import random_program, program_seed
+    prog = random_program(a.big_atoms, 4 * a.big_atoms, program_seed(2, 7))
+    P = aspgpu.Program(prog, conflict_budget=a.big_conflicts, time_budget_ms=60_000)
+    st = P.stats()
+    stream = torch.cuda.current_stream(dev)
+    nonunit = st["n_nogoods"] - st["n_unit_nogoods"]
+    sweep_bytes = 4 * (st["n_literals"] - st["n_unit_nogoods"]) + 4 * nonunit
+
+    def timed(passes, reps=5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        P.sweep(passes)
+        e0.record(stream)
+        for _ in range(reps):
+            P.sweep(passes)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    K = 16
+    t1, tk = timed(1), timed(K + 1)
+    per_pass = (tk - t1) / K
+    sw_gbs = sweep_bytes / (per_pass / 1e3) / 1e9
+    P.solve(1, cap=1)                                    # warm-up solve
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    status, _, _ = P.solve(1, cap=1)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    s = P.stats()
+    dev_ms = s["ns_total"] / 1e6
+    alg = 4.0 * s["literal_checks"] + 4.0 * s["nogood_visits"]
+    out = {"workload": f"random program, {a.big_atoms // 1000}k atoms, {4 * a.big_atoms // 1000}k rules, "
+                       f"body 1-4, negation 0.5; store {st['store_bytes'] / 1e6:.0f} MB (> 126 MB L2)",
+           "store_bytes": st["store_bytes"], "nogoods": st["n_nogoods"], "literals": st["n_literals"],
+           "sweep": {"ms_per_pass": per_pass, "bytes_per_pass": sweep_bytes, "achieved_gbs": sw_gbs,
+                     "frac_of_hbm": sw_gbs / peak if peak else None,
+                     "note": "standalone sweep_kernel, (t(17 passes) - t(1 pass)) / 16, CUDA events"},
+           "solver": {"status": int(status), "conflict_budget": a.big_conflicts, "device_ms": dev_ms,
+                      "event_ms": ms, "literal_checks": s["literal_checks"], "nogood_visits": s["nogood_visits"],
+                      "achieved_gbs": alg / (dev_ms / 1e3) / 1e9,
+                      "frac_of_hbm": alg / (dev_ms / 1e3) / 1e9 / peak if peak else None,
+                      "frac_4B_per_check": 4.0 * s["literal_checks"] / (dev_ms / 1e3) / 1e9 / peak if peak else None,
+                      "rounds_per_s": s["rounds"] / (dev_ms / 1e3),
+                      "decisions_per_s": s["decisions"] / (dev_ms / 1e3)}}
+    P.close()
+    return out
+
+
+def _tiny(a, aspgpu, torch):
+    """Tiny programs (20 atoms, 40 rules, 3 constraints; seeds 0..N-1): all
+    answer sets of every program, batched (one launch) and one at a time;
+    the oracle's brute force over 2^20 interpretations on a sample."""
+    import oracle
+    from synth.programs import tiny_program
+    progs = [tiny_program(i) for i in range(a.tiny)]
+    P = [aspgpu.Program(p) for p in progs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, nm, _ = aspgpu.solve_batch(P, max_models_each=0, cap_each=64)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    n_plain = 0
+    for q in P:
+        _, _, n = q.solve(0, cap=64)
+        n_plain += n
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    for q in P:
+        q.close()
+    sample = progs[:8]
+    t0 = time.perf_counter()
+    n_bf = sum(len(oracle.brute_force(p)) for p in sample)
+    tbf = time.perf_counter() - t0
+    return {"workload": f"{a.tiny} tiny programs (20 atoms, 40 rules, 3 constraints), every answer set",
+            "answer_sets": int(nm.sum()), "answer_sets_plain": int(n_plain),
+            "batched": {"seconds": tb, "instances_per_s": a.tiny / tb},
+            "plain": {"seconds": tp, "instances_per_s": a.tiny / tp},
+            "cpu_baseline": {"kind": "oracle brute force over 2^20 interpretations", "cores": 1,
+                             "sample": f"first {len(sample)} programs ({n_bf} answer sets)",
+                             "instances_per_s": len(sample) / tbf}}
+
+
+def _work_ratios(out):
+    """Rates of the same search work against the oracle on one core (the
+    literal-check ratio compares different work: the sweeps re-read the whole
+    store, the oracle reads occurrence lists)."""
+    s, c = out.get("search"), out.get("cpu_baseline")
+    if not s or not c:
+        return None
+    return {k: s[k] / c[k] if c.get(k) else None for k in ("decisions_per_s", "propagations_per_s", "conflicts_per_s")}
+
+
+def _summary(out):
+    """The headline figures of every leg, compact (the end of the line)."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict):
+                return None
+            d = d.get(k)
+        return round(d, 4) if isinstance(d, float) else d
+    return {
+        "checks_per_s": g(out, "value"), "frac_hbm": g(out, "roofline", "frac"),
+        "decisions_per_s": g(out, "search", "decisions_per_s"),
+        "propagations_per_s": g(out, "search", "propagations_per_s"),
+        "work_vs_oracle": out.get("work_vs_oracle"),
+        "big_store_sweep_frac": g(out, "big_store", "sweep", "frac_of_hbm"),
+        "big_store_solver_frac": g(out, "big_store", "solver", "frac_of_hbm"),
+        "tiny_instances_per_s": [g(out, "tiny_programs", "batched", "instances_per_s"),
+                                 g(out, "tiny_programs", "plain", "instances_per_s")],
+        "batched_solved": [g(out, "batched", "batched", "solved"), g(out, "batched", "plain", "solved"),
+                           g(out, "batched", "oracle_all_cores", "solved")],
+        "batched_speedup": g(out, "batched", "speedup_solved_per_s"),
+        "batched_oracle_mismatches": g(out, "batched", "oracle_all_cores", "status_mismatches"),
+        "learned_solved": [g(out, "learned_heuristic", "plain", "solved"),
+                           g(out, "learned_heuristic", "learned", "solved"),
+                           g(out, "learned_heuristic", "learned_static", "solved")],
+        "learned_speedup": [g(out, "learned_heuristic", "speedup_solved_per_s"),
+                            g(out, "learned_heuristic", "speedup_static_solved_per_s")],
+        "frontier_decisions_per_s": {k: g(out, "frontier_compare", k, "decisions_per_s")
+                                     for k in ("full", "nogoods", "units")},
+    }
 
 
 def _a11_programs(count, first_index):
@@ -470,7 +699,7 @@ def _learned(a, aspgpu, torch):
     same per-program conflict budget; training on traces of the plain
     heuristic on disjoint seeds."""
     from paper_1909_01786_gb300 import heuristic as H
-    budget = a.batch_conflicts
+    budget = a.learned_conflicts
     t0 = time.perf_counter()
     X, y = H.collect_traces(_a11_programs(a.learned_train, 10**6), conflict_budget=budget)
     w, tstats = H.fit(X, y)
@@ -529,7 +758,7 @@ def _search_options(a, aspgpu, torch):
     the learned-heuristic comparison."""
     import oracle
     evalp = _a11_programs(a.learned, 2 * 10**6)
-    budget = a.batch_conflicts
+    budget = a.learned_conflicts
     modes = (("fwd, backjump h-1 (default)", dict()),
              ("fwd, asserting backjump", dict(backjump=aspgpu.BACKJUMP_ASSERTING)),
              ("fwd, Luby restarts x16", dict(restart_conflicts=16)),

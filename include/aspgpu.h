@@ -89,6 +89,18 @@ extern "C" {
 #define ASP_LEARN_FWD 0
 #define ASP_LEARN_RES 1
 
+/* Propagation rounds (Section 4.1; Algorithm 2 checks only the nogoods of
+ * the literals assigned last).  FULL: every round sweeps every nogood.
+ * NOGOODS: a round checks the nogoods holding a variable assigned in the
+ * previous round, one lane per nogood from per-variable occurrence lists.
+ * UNITS: a round sweeps the units of the static partition (32-nogood groups
+ * of one bucket, as full sweeps take them) that hold a variable assigned in
+ * the previous round; a claim marks them in a dirty bitmap for the next
+ * round (single-program solving; a batch sweeps everything). */
+#define ASP_FRONTIER_FULL 0
+#define ASP_FRONTIER_NOGOODS 1
+#define ASP_FRONTIER_UNITS 2
+
 /* Backjump target of fwd-learning, with h the highest level in the
  * conflict's dependency bitmap.  H_MINUS_1: level h-1 (Algorithm 4's
  * reading).  ASSERTING: the second-highest level in the bitmap (1 if there
@@ -126,10 +138,9 @@ typedef struct {
     /* ASP_VIEW_*: the widest view allowed (a wider one than fits in shared
        memory falls back to the next narrower); 0 = ASP_VIEW_AUTO */
     int32_t view_mode;
-    /* 1: frontier propagation -- a round checks only the nogoods of the
-       variables assigned in the previous round (Algorithm 2's frontier;
-       nogood-by-variable occurrence lists built at load), full sweeps after
-       backjumps; 0: every round sweeps every nogood */
+    /* ASP_FRONTIER_*: which static nogoods a propagation round checks
+       (Algorithm 2's frontier idea; the long and learned nogoods are checked
+       every round, and rounds after backjumps sweep everything) */
     int32_t frontier;
     /* ASP_LEARN_*: conflict analysis */
     int32_t learning;

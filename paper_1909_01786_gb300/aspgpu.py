@@ -21,6 +21,7 @@ HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED, HEUR_LEARNED_STATIC, HEUR_JW = 0, 
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 VIEW_AUTO, VIEW_PLAIN, VIEW_PACKED, VIEW_BYTES = 0, 1, 2, 3
 LEARN_FWD, LEARN_RES = 0, 1
+FRONTIER_FULL, FRONTIER_NOGOODS, FRONTIER_UNITS = 0, 1, 2
 BACKJUMP_H_MINUS_1, BACKJUMP_ASSERTING = 0, 1
 R_DECISION, R_COMPLETE, R_INPUT = 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD
 
@@ -187,7 +188,7 @@ class Program:
             opt.mlp_weights = w.ctypes.data
         opt.trace_capacity = int(trace_capacity)
         opt.view_mode = int(view_mode)
-        opt.frontier = 1 if frontier else 0
+        opt.frontier = int(frontier)         # False/True = full / nogood frontier; FRONTIER_UNITS
         opt.learning = int(learning)
         opt.backjump = int(backjump)
         opt.restart_conflicts = int(restart_conflicts)

@@ -44,6 +44,14 @@ static int cuda_fail(cudaError_t e, const char *what)
     return fail(ASP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// device arrays of a frontier by units (see unit_lists)
+struct UnitLists {
+    const uint32_t *ubase = nullptr, *uoff = nullptr, *unit = nullptr;
+    uint32_t *dirty = nullptr;
+    uint32_t words = 0;
+    bool built = false;
+};
+
 struct asp_prog {
     asp_options opt{};
     cudaStream_t stream = nullptr;
@@ -57,6 +65,7 @@ struct asp_prog {
     // the same program as one CTA solves it in a batch, for each batch
     // kernel configuration (256 threads, 3 per SM; 128 threads, 6 per SM)
     Dev D1[2]{};
+    UnitLists batch_units;              // frontier by units in batches
     size_t smem1[2] = {0, 0};
     int64_t n_nogoods = 0, n_literals = 0, n_units = 0, n_long = 0, store_bytes = 0;
     bool empty_nogood = false;
@@ -192,6 +201,87 @@ static int choose_view(asp_prog *p, const HostStore &H, Dev &D, const std::vecto
     return ASP_OK;
 }
 
+// Frontier by units (frontier = 2) over a static partition of G CTAs
+// (bucket L's nogoods [boff[L*(G+1)+g], boff[L*(G+1)+g+1]) belong to CTA
+// g): the sweep units numbered globally (CTA g's units are [ubase[g],
+// ubase[g+1]), in the order the device's unit table gives them: bucket by
+// bucket, unit_groups(L) groups of 32 nogoods each), for every variable the
+// units whose nogoods hold it, and the two dirty bitmaps.  Sets *built =
+// false (and allocates nothing) if the partition has more than max_units.
+
+static int unit_lists(asp_prog *p, const HostStore &H, const std::vector<uint32_t> &boff, uint32_t G,
+                      uint64_t max_units, UnitLists &out)
+{
+    const Dev &D = p->D;
+    const uint32_t G1 = G + 1u;
+    std::vector<uint32_t> ubase(G1, 0u), lbase((size_t)G * (BUCKET_MAX + 1), 0u);
+    for (uint32_t c = 0; c < G; c++) {
+        uint32_t acc = 0;
+        for (int L = 2; L <= BUCKET_MAX; L++) {
+            lbase[(size_t)c * (BUCKET_MAX + 1) + L] = acc;
+            const uint32_t n = boff[L * G1 + c + 1] - boff[L * G1 + c];
+            const uint32_t groups = (n + 31u) >> 5, per = unit_groups((uint32_t)L);
+            acc += (groups + per - 1u) / per;
+        }
+        ubase[c + 1] = ubase[c] + acc;
+    }
+    const uint32_t total = ubase[G];
+    out.built = false;
+    if (total > max_units) return ASP_OK;
+    // every (variable, unit) pair once: nogoods are visited in unit order,
+    // so a repeat of a pair is always adjacent to its first visit
+    std::vector<uint32_t> off((size_t)D.nv + 1, 0u), last((size_t)D.nv, 0xFFFFFFFFu), occ;
+    for (int pass = 0; pass < 2; pass++) {
+        std::fill(last.begin(), last.end(), 0xFFFFFFFFu);
+        std::vector<uint32_t> fill;
+        if (pass == 1) {
+            for (uint32_t v = 0; v < D.nv; v++) off[v + 1] += off[v];
+            occ.resize(off[D.nv]);
+            fill.assign(off.begin(), off.end() - 1);
+        }
+        for (uint32_t c = 0; c < G; c++) {
+            for (int L = 2; L <= BUCKET_MAX; L++) {
+                const std::vector<uint32_t> &rows = H.bucket_rows[L];
+                const uint32_t k0 = boff[L * G1 + c], k1 = boff[L * G1 + c + 1];
+                const uint32_t first = ubase[c] + lbase[(size_t)c * (BUCKET_MAX + 1) + L];
+                const uint32_t per = unit_groups((uint32_t)L) * 32u;
+                for (uint32_t k = k0; k < k1; k++) {
+                    const uint32_t u = first + (k - k0) / per;
+                    for (int q = 0; q < L; q++) {
+                        const uint32_t v = rows[(size_t)k * L + q] >> 1;
+                        if (last[v] == u) continue;
+                        last[v] = u;
+                        if (pass == 0) off[v + 1]++;
+                        else occ[fill[v]++] = u;
+                    }
+                }
+            }
+        }
+    }
+    int rc = ASP_OK;
+    out.ubase = upload(p, ubase, rc);
+    if (rc == ASP_OK) out.uoff = upload(p, off, rc);
+    if (rc == ASP_OK) out.unit = upload(p, occ, rc);
+    if (rc != ASP_OK) return rc;
+    out.words = (total + 31u) / 32u + 1u;
+    out.dirty = (uint32_t *)dalloc(p, (size_t)out.words * 2 * 4);
+    if (!out.dirty) return fail(ASP_E_OOM, "device allocation failed (dirty bitmaps)");
+    cudaError_t e = cudaMemsetAsync(out.dirty, 0, (size_t)out.words * 2 * 4, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clear dirty bitmaps");
+    out.built = true;
+    return ASP_OK;
+}
+
+static void use_unit_lists(Dev &D, const UnitLists &U)
+{
+    D.frontier = U.built ? 2u : 0u;
+    D.cta_ubase = U.ubase;
+    D.occ_uoff = U.uoff;
+    D.occ_unit = U.unit;
+    D.dirty = U.dirty;
+    D.dirty_words = U.words;
+}
+
 // Grid size, the static partition of the buckets over the CTAs along groups
 // (an atom with its rules; a constraint), each CTA's slice of auxiliary
 // variables kept in shared memory, and the shared-memory layout.
@@ -248,6 +338,12 @@ static int plan_grid(asp_prog *p, const HostStore &H)
     int rc = choose_view(p, H, D, boff, alo, an, base_smem, max_smem);
     if (rc != ASP_OK) return rc;
     p->smem = base_smem + 4 * D.view_words;
+    if (D.frontier == 2) {
+        UnitLists U;
+        rc = unit_lists(p, H, boff, D.G, ~0ull, U);
+        if (rc != ASP_OK) return rc;
+        use_unit_lists(D, U);
+    }
     D.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D.cta_auxn = upload(p, an, rc);
@@ -264,6 +360,8 @@ static int plan_grid(asp_prog *p, const HostStore &H)
 // configuration (3 or 6 CTAs in an SM's 228 KB, less reserved and static
 // shared memory).
 constexpr size_t BATCH_SMEM_BUDGET[2] = {72 * 1024 - 1024, 34 * 1024};
+// frontier by units in batches: programs of at most this many sweep units
+constexpr uint64_t BATCH_MAX_UNITS = 1u << 16;
 
 static int plan_batch(asp_prog *p, const HostStore &H, int config)
 {
@@ -279,6 +377,13 @@ static int plan_batch(asp_prog *p, const HostStore &H, int config)
     D1.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D1.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D1.cta_auxn = upload(p, an, rc);
+    if (rc == ASP_OK && p->D.frontier == 2) {
+        // one program per CTA: the units of the whole store (the same for
+        // both configurations); programs too large for batches keep full
+        // sweeps there
+        if (config == 0) rc = unit_lists(p, H, boff, 1u, BATCH_MAX_UNITS, p->batch_units);
+        if (rc == ASP_OK) use_unit_lists(D1, p->batch_units);
+    }
     p->D1[config] = D1;
     p->smem1[config] = base + 4 * D1.view_words;
     return rc;
@@ -484,6 +589,8 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
         return fail(ASP_E_ARG, "conflicts_per_round must be 0..4");
     }
     D.conf_per_round = (uint32_t)std::max(1, p->opt.conflicts_per_round);
+    if (p->opt.frontier < 0 || p->opt.frontier > 2) { delete p; return fail(ASP_E_ARG, "unknown frontier mode"); }
+    D.frontier = (uint32_t)p->opt.frontier;
     D.stall_cta = 0xFFFFFFFFu;
     D.barrier_ns = 20000000000ull;
     p->n_nogoods = H.n_nogoods;
@@ -577,7 +684,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
             if (e != cudaSuccess) rc = cuda_fail(e, "clear stamps");
         }
     }
-    if (rc == ASP_OK && p->opt.frontier) {
+    if (rc == ASP_OK && p->opt.frontier == 1) {
         // per variable, the ids of the bucket nogoods it occurs in
         std::vector<uint32_t> off((size_t)D.nv + 1, 0), occ;
         for (int L = 2; L <= BUCKET_MAX; L++) {
@@ -637,6 +744,7 @@ static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t m
     if (e == cudaSuccess) e = cudaMemsetAsync(D.stats, 0, sizeof(DevStats), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.bar, 0, sizeof(Barrier), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.level_start, 0, ((size_t)D.J + 4) * 4, st);
+    if (e == cudaSuccess && D.dirty) e = cudaMemsetAsync(D.dirty, 0, (size_t)D.dirty_words * 2 * 4, st);
     static thread_local Ctl ctl[2];
     static thread_local Acc acc[4];
     std::memset(ctl, 0, sizeof(ctl));
@@ -647,7 +755,7 @@ static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t m
     ctl[0].lfill = D.lits_static;
     for (int i = 0; i < 4; i++) {
         acc[i].ckey = NO_KEY; acc[i].cslot[0] = acc[i].cslot[1] = acc[i].cslot[2] = NO_KEY; acc[i].dkey = 0; acc[i].nclaim = 0; acc[i].flag = 0;
-        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0; acc[i].tbusy = 0; acc[i].tsweep = 0;
+        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0; acc[i].visits = 0; acc[i].tbusy = 0; acc[i].tsweep = 0;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.acc, acc, sizeof(acc), cudaMemcpyHostToDevice, st);
@@ -812,7 +920,7 @@ int asp_sweep(asp_prog *p, int32_t passes)
     if (!p || passes < 1) return fail(ASP_E_ARG, "bad argument");
     Acc a;
     a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY;
-    a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0;
+    a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.visits = 0;
     a.tbusy = 0; a.tsweep = 0;
     cudaError_t e = cudaMemcpyAsync(p->d_sweep_acc, &a, sizeof(a), cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep reset");

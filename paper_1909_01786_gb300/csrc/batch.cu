@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *d
         for (uint32_t w = threadIdx.x; w <= D.asg_words; w += blockDim.x) D.asg[w] = 0u;
         for (uint32_t v = threadIdx.x; v < D.nv; v += blockDim.x) D.dl[v] = 0;
         for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) D.act[j] = 0u;
+        if (D.frontier == 2u)
+            for (uint32_t w = threadIdx.x; w < 2u * D.dirty_words; w += blockDim.x) D.dirty[w] = 0u;
         if (threadIdx.x == 0) {
             Ctl c;
             memset(&c, 0, sizeof(c));
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *d
             memset(&c, 0, sizeof(c));
             D.ctl[1] = c;
             Acc a;
-            a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.tbusy = 0; a.tsweep = 0;
+            a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.visits = 0; a.tbusy = 0; a.tsweep = 0;
             for (int i = 0; i < 4; i++) D.acc[i] = a;
             memset(D.stats, 0, sizeof(DevStats));
             memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check

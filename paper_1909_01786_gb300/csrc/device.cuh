@@ -76,7 +76,9 @@ struct Acc {              // per-phase accumulators, indexed by phase % 4
     uint32_t flag;              // something changed (least-model iteration)
     uint32_t minU;              // smallest unfounded true atom
     uint32_t nlits;             // literals appended to the loop nogood
-    unsigned long long checks;  // literals classified by long/learned sweeps
+    unsigned long long checks;  // literals classified by long/learned sweeps (and by unit
+                                // frontiers' bucket units)
+    unsigned long long visits;  // bucket nogoods classified by unit frontiers
     unsigned long long tbusy;   // max over CTAs of the time from phase start to barrier arrival
     unsigned long long tsweep;  // max over CTAs of the time in the sweep
 };
@@ -163,6 +165,16 @@ struct Dev {
     // occurs in); full sweeps after (re)starts and backjumps
     uint32_t frontier;
     const uint32_t *occ_off, *occ;
+    // frontier = 2 (frontier by bucket units): the sweep units of the static
+    // partition are numbered globally, CTA g's being [cta_ubase[g],
+    // cta_ubase[g+1]); occ_unit[occ_uoff[v] .. occ_uoff[v+1]) are the units
+    // whose nogoods hold variable v.  A claim sets the bits of v's units in
+    // the next round's dirty bitmap (two bitmaps of dirty_words words,
+    // alternating by round); each round's sweep checks the units whose bit
+    // is set and clears them.
+    const uint32_t *cta_ubase, *occ_uoff, *occ_unit;
+    uint32_t *dirty;
+    uint32_t dirty_words, pad3;
     uint32_t *asg;
     int32_t *dl;
     uint32_t *reason;

@@ -327,6 +327,8 @@ struct SweepCtx {
     // inside a sweep: claims are listed in shared memory and copied to the
     // trail once at the end of the sweep (one global atomic per CTA)
     bool listed = false;
+    // frontier by units: the next round's dirty bitmap (null otherwise)
+    uint32_t *dmark = nullptr;
 };
 
 constexpr uint32_t CLAIM_BUF = 256;
@@ -343,6 +345,54 @@ __shared__ unsigned int s_unit, s_unit2[2];
 // CTA 0, thread 0: time in the sweeps on long and learned nogoods and on
 // the buckets
 __shared__ unsigned long long s_tlearned, s_tbuckets;
+// frontier by units (single-program solver only): this round's queue of the
+// CTA's bucket units (local unit indices) and its length
+constexpr uint32_t DQ_CAP = 1024;
+__shared__ uint32_t s_dq[DQ_CAP];
+__shared__ unsigned int s_nq;
+
+// Frontier by units: this CTA's bucket units to check in the round -- those
+// whose bit is set in the round's dirty bitmap `buf` (set by the claims of
+// the previous claiming phase; the bits read are cleared) and, in a decision
+// phase, those holding the decision variable dec_v.  Warp 0 writes the queue
+// (s_nq > DQ_CAP: it overflowed, and the CTA sweeps all its units); the
+// caller synchronises the CTA before the sweep.
+__device__ __forceinline__ void build_unit_queue(const Dev &D, uint32_t cta, uint32_t *buf, uint32_t dec_v)
+{
+    if (threadIdx.x >= 32u) return;
+    const uint32_t lane = threadIdx.x;
+    const uint32_t ub0 = __ldg(D.cta_ubase + cta), ub1 = __ldg(D.cta_ubase + cta + 1u);
+    if (ub1 > ub0) {
+        const uint32_t w_first = ub0 >> 5, w_last = (ub1 - 1u) >> 5;
+        for (uint32_t w0 = w_first; w0 <= w_last; w0 += 32u) {
+            const uint32_t w = w0 + lane;
+            uint32_t bits = 0u;
+            if (w <= w_last) {
+                uint32_t own = ~0u;
+                if (w == w_first) own &= ~0u << (ub0 & 31u);
+                if (w == w_last && (ub1 & 31u)) own &= (1u << (ub1 & 31u)) - 1u;
+                bits = __ldcg(buf + w) & own;
+                if (bits) atomicAnd(buf + w, ~bits);
+            }
+            while (bits) {
+                const uint32_t b = (uint32_t)__ffs(bits) - 1u;
+                bits &= bits - 1u;
+                const uint32_t pos = atomicAdd(&s_nq, 1u);
+                if (pos < DQ_CAP) s_dq[pos] = w * 32u + b - ub0;
+            }
+        }
+    }
+    if (dec_v != 0xFFFFFFFFu) {
+        const uint32_t o0 = __ldg(D.occ_uoff + dec_v), o1 = __ldg(D.occ_uoff + dec_v + 1u);
+        for (uint32_t o = o0 + lane; o < o1; o += 32u) {
+            const uint32_t u = __ldg(D.occ_unit + o);
+            if (u >= ub0 && u < ub1) {
+                const uint32_t pos = atomicAdd(&s_nq, 1u);
+                if (pos < DQ_CAP) s_dq[pos] = u - ub0;
+            }
+        }
+    }
+}
 
 __device__ __forceinline__ void report_conflict(const SweepCtx &X, uint32_t id, uint32_t len)
 {
@@ -366,6 +416,33 @@ __device__ __forceinline__ void record_claim(const SweepCtx &X, uint32_t v, uint
     if (pos < D.nv) {
         D.trail[pos] = entry;
         if (D.tpos) D.tpos[v] = pos;
+    }
+}
+
+// Frontier by units: the bucket units holding variable x are checked in the
+// next round; set their bits in that round's dirty bitmap.  All 32 lanes call
+// it with the same x.
+__device__ __forceinline__ void warp_mark_units(const SweepCtx &X, uint32_t x)
+{
+    if (!X.dmark) return;
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t o0 = __ldg(D.occ_uoff + x), o1 = __ldg(D.occ_uoff + x + 1u);
+    for (uint32_t o = o0 + lane; o < o1; o += 32u) {
+        const uint32_t u = __ldg(D.occ_unit + o);
+        atomicOr(X.dmark + (u >> 5), 1u << (u & 31u));
+    }
+}
+
+// The same from one lane.
+__device__ __forceinline__ void lane_mark_units(const SweepCtx &X, uint32_t x)
+{
+    if (!X.dmark) return;
+    const Dev &D = *X.D;
+    const uint32_t o0 = __ldg(D.occ_uoff + x), o1 = __ldg(D.occ_uoff + x + 1u);
+    for (uint32_t o = o0; o < o1; o++) {
+        const uint32_t u = __ldg(D.occ_unit + o);
+        atomicOr(X.dmark + (u >> 5), 1u << (u & 31u));
     }
 }
 
@@ -535,6 +612,7 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
             if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
             if (r != 0) continue;
             record_claim(X, x, valbit, id);
+            lane_mark_units(X, x);
             if (X.cdl > 1u) {
                 uint32_t var[L];
 #pragma unroll
@@ -627,24 +705,32 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
                     }
                 }
             }
-            if (L > 8 && won && X.cdl > 1u) {
+            if (L > 8 && won) {
                 // long buckets (few claims): the claiming lane alone
-                uint32_t var[L];
+                lane_mark_units(X, x);
+                if (X.cdl > 1u) {
+                    uint32_t var[L];
 #pragma unroll
-                for (int q = 0; q < L; q++) var[q] = X.V.var(lit[t][q] >> 2);
-                lane_deps<L>(X, var, x);
+                    for (int q = 0; q < L; q++) var[q] = X.V.var(lit[t][q] >> 2);
+                    lane_deps<L>(X, var, x);
+                }
             }
-            if (L <= 8 && X.cdl > 1u) {
-                // bitmaps of this group's claims, one claim at a time, by the warp
+            if (L <= 8 && (X.cdl > 1u || X.dmark)) {
+                // bitmaps (and unit marks) of this group's claims, one claim
+                // at a time, by the warp
                 unsigned m = __ballot_sync(FULL_MASK, won);
                 if (m) {
                     while (m) {
                         const int src = __ffs(m) - 1;
                         m &= m - 1u;
-                        uint32_t var[L];
+                        const uint32_t xs = __shfl_sync(FULL_MASK, x, src);
+                        warp_mark_units(X, xs);
+                        if (X.cdl > 1u) {
+                            uint32_t var[L];
 #pragma unroll
-                        for (int q = 0; q < L; q++) var[q] = X.V.var(__shfl_sync(FULL_MASK, lit[t][q], src) >> 2);
-                        warp_deps<L>(X, var, __shfl_sync(FULL_MASK, x, src));
+                            for (int q = 0; q < L; q++) var[q] = X.V.var(__shfl_sync(FULL_MASK, lit[t][q], src) >> 2);
+                            warp_deps<L>(X, var, xs);
+                        }
                     }
                     __threadfence_block();
                     __syncwarp();
@@ -660,9 +746,6 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
     }
 }
 
-// Groups of 32 nogoods per unit of work, by bucket length: about 16 literal
-// loads in flight per lane.
-__host__ __device__ constexpr uint32_t unit_groups(uint32_t L) { return L <= 2u ? 8u : L <= 4u ? 4u : L <= 8u ? 2u : 1u; }
 
 template <bool BYTES>
 __device__ __forceinline__ void run_unit_view(const SweepCtx &X, uint32_t L, uint32_t k0, uint32_t k1)
@@ -764,6 +847,7 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
     won = __shfl_sync(FULL_MASK, won, 0);
     if (!won) return;
     const uint32_t x = ulit >> 1;
+    warp_mark_units(X, x);
     if (X.cdl > 1u) {
         __threadfence_block();
         bool first = true;
@@ -869,6 +953,7 @@ __device__ __forceinline__ void unit_table(const Dev &D, uint32_t cta)
     if (threadIdx.x != 0) return;
     s_unit = 0u;
     s_ncl = 0u;
+    s_nq = 0u;
     s_unit2[0] = 0u;
     s_unit2[1] = 0u;
     const uint32_t G1 = D.G + 1u;
@@ -884,10 +969,17 @@ __device__ __forceinline__ void unit_table(const Dev &D, uint32_t cta)
     s_ubase[BUCKET_MAX + 1] = acc;
 }
 
-// Propagate-and-check over this CTA's ranges of every bucket, then
-// (grid-wide) the static long nogoods and the learned nogoods.
+// Propagate-and-check over this CTA's ranges of every bucket (full), or
+// over the frontier -- the nogoods of the previous round's assignments
+// (frontier = 1) or the dirty bucket units (frontier = 2), taken from the
+// CTA's queue (DQ = 1, the single-program solver) or straight from the
+// round's dirty bitmap, one 32-unit word per warp (DQ = 2, one program per
+// CTA: every word belongs to the CTA) -- then (grid-wide) the static long
+// nogoods and the learned nogoods.  dbuf: the round's dirty bitmap (DQ = 2).
+template <int DQ>
 __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bool full = true,
-                                      uint32_t fr0 = 0u, uint32_t fr1 = 0u, uint32_t pass = 0u)
+                                      uint32_t fr0 = 0u, uint32_t fr1 = 0u, uint32_t pass = 0u,
+                                      uint32_t *dbuf = nullptr)
 {
     SweepCtx X = X0;
     // Listed claims take their trail slots at the end of the sweep, after
@@ -917,7 +1009,27 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         uctr = &s_unit2[pass & 1u];
     }
     const uint32_t *const ubase = s_ubase;     // set up once per launch (unit_table)
-    const uint32_t units = full ? ubase[BUCKET_MAX + 1] : 0u;
+    uint32_t units = full ? ubase[BUCKET_MAX + 1] : 0u;
+    // frontier by units: the queue (or, if it overflowed, every unit of the
+    // CTA); the literals and nogoods of the units checked are counted here
+    bool queued = false, count_units = false, words = false;
+    if constexpr (DQ == 1) {
+        if (!full && D.frontier == 2u) {
+            const uint32_t nq = s_nq;
+            queued = nq <= DQ_CAP;
+            units = queued ? nq : ubase[BUCKET_MAX + 1];
+            count_units = true;
+        }
+    }
+    if constexpr (DQ == 2) {
+        if (!full && D.frontier == 2u) {
+            words = true;
+            units = D.dirty_words;
+            count_units = true;
+        }
+    }
+    uint32_t pending = 0u, wbase = 0u;        // DQ = 2: units of the warp's word not yet run
+    unsigned long long uvisits = 0;
     // Long and learned nogoods first (one warp each, round-robin over CTAs
     // first, then over the warps of a CTA); the warps that take one then
     // take fewer bucket units from the queue.
@@ -931,9 +1043,27 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
     for (;;) {
         uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(uctr, 1u);
-        u = __shfl_sync(FULL_MASK, u, 0);
-        if (u >= units) break;
+        if (words && pending) {
+            u = wbase + (uint32_t)__ffs(pending) - 1u;
+            pending &= pending - 1u;
+        } else {
+            if (lane == 0) u = atomicAdd(uctr, 1u);
+            u = __shfl_sync(FULL_MASK, u, 0);
+            if (u >= units) break;
+            if constexpr (DQ == 1) {
+                if (queued) u = s_dq[u];
+            }
+            if constexpr (DQ == 2) {
+                if (words) {
+                    // take the word's bits and clear them in one atomic
+                    uint32_t b = 0u;
+                    if (lane == 0) b = atomicExch(dbuf + u, 0u);
+                    pending = __shfl_sync(FULL_MASK, b, 0);
+                    wbase = u * 32u;
+                    continue;
+                }
+            }
+        }
         uint32_t L = 2;
 #pragma unroll
         for (uint32_t q = 3; q <= (uint32_t)BUCKET_MAX; q++)
@@ -944,13 +1074,19 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         if (D.view_mode == VIEW_BYTES) run_unit_view<true>(X, L, k0, b1);
         else if (D.view_mode == VIEW_PACKED) run_unit_view<false>(X, L, k0, b1);
         else run_unit(X, L, k0, b1);
+        if (count_units && lane == 0) {
+            const uint32_t n = min(b1 - k0, unit_groups(L) * 32u);
+            checks += (unsigned long long)L * n;
+            uvisits += n;
+        }
     }
-    if (!full) {
+    if (!full && D.frontier == 1u) {
         unsigned long long fchecks = 0;           // per lane (classify_long's are per warp)
         frontier_round(X, fr0, fr1, fchecks);
         checks += __reduce_add_sync(FULL_MASK, (unsigned)fchecks);
     }
     if (lane == 0 && checks) atomicAdd(&X.acc->checks, checks);
+    if (lane == 0 && uvisits) atomicAdd(&X.acc->visits, uvisits);
     if (timer) {
         const unsigned long long t2 = globaltimer_ns();
         s_tlearned += t1 - t0;
@@ -961,7 +1097,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         // then every thread copies (no barrier under a data-dependent branch)
         cta_sync();
         const uint32_t n = min(s_ncl, CLAIM_BUF);
-        if (threadIdx.x == 0) s_unit = 0u;          // every warp has left the unit queue
+        if (threadIdx.x == 0) { s_unit = 0u; s_nq = 0u; }   // every warp has left the unit queue
         if (threadIdx.x < 32u) {
             uint32_t base = 0;
             if (threadIdx.x == 0 && n) base = atomicAdd(&X.acc->nclaim, n);
@@ -1735,6 +1871,10 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 if (leader) N.op = OP_APPLY;
                 break;
             }
+            // frontier by units: this round's dirty units of the CTA
+            if constexpr (!BATCH) {
+                if (D.frontier == 2u) build_unit_queue(D, cta, D.dirty + (C.round & 1u) * D.dirty_words, 0xFFFFFFFFu);
+            }
             // make last round's claims visible: clear their fresh bit
             // (grid-wide) and put them in this CTA's view
             for (uint32_t i = C.tc + gtid; i < tend; i += nthreads) {
@@ -1752,7 +1892,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             cta_sync();
             sw = true; sw_cdl = C.cdl; sw_tbase = tend;
-            sw_full = C.full != 0u || !D.frontier;
+            sw_full = C.full != 0u || D.frontier == 0u;
             sw_fr0 = C.tc; sw_fr1 = tend;
             if (leader) {
                 N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1; N.full = 0;
@@ -1780,7 +1920,10 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     }
                 }
                 if (leader) {
-                    N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = tend; N.clean = 0; N.full = 0;
+                    // (frontier by units: completion claims mark no units, so
+                    // the next round sweeps everything)
+                    N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = tend; N.clean = 0;
+                    N.full = D.frontier == 2u ? 1u : 0u;
                     atomicAdd(&D.stats->completions, 1ull);
                 }
                 break;
@@ -1802,9 +1945,23 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 atomicOr(D.asg + (bv >> 3), V_T << ((bv & 7u) * 4u));
             }
             if (threadIdx.x == 0) view_set(V, bv, V_T);
+            if (D.frontier == 2u) {
+                uint32_t *buf = D.dirty + (C.round & 1u) * D.dirty_words;
+                if constexpr (!BATCH) {
+                    build_unit_queue(D, cta, buf, bv);
+                } else if (threadIdx.x < 32u) {
+                    // one program per CTA: the decision variable's units go
+                    // into the bitmap the sweep takes its words from
+                    const uint32_t o0 = __ldg(D.occ_uoff + bv), o1 = __ldg(D.occ_uoff + bv + 1u);
+                    for (uint32_t o = o0 + threadIdx.x; o < o1; o += 32u) {
+                        const uint32_t u = __ldg(D.occ_unit + o);
+                        atomicOr(buf + (u >> 5), 1u << (u & 31u));
+                    }
+                }
+            }
             cta_sync();
             sw = true; sw_cdl = L; sw_tbase = tend + 1u; sw_dec = bv;
-            sw_full = !D.frontier;
+            sw_full = D.frontier == 0u;
             if (leader) {
                 N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
                 N.clean = 0; N.full = 0;
@@ -2007,7 +2164,9 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         if (sw) {
             const unsigned long long ts = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
             SweepCtx X{&D, V, fresh_cur, sw_cdl, sw_tbase, acc, true, true, sw_dec, cta, rank >> 5, size >> 5};
-            sweep(X, C.n_learned, sw_full, sw_fr0, sw_fr1);
+            if (D.frontier == 2u) X.dmark = D.dirty + ((C.round + 1u) & 1u) * D.dirty_words;
+            sweep<BATCH ? 2 : 1>(X, C.n_learned, sw_full, sw_fr0, sw_fr1, 0u,
+                                 D.frontier == 2u ? D.dirty + (C.round & 1u) * D.dirty_words : nullptr);
             if (threadIdx.x == 0) atomicMax(&acc->tsweep, globaltimer_ns() - ts);
         }
 
@@ -2020,11 +2179,12 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             D.ctl[(k + 1u) & 1u] = N;
             Acc z;
-            z.ckey = NO_KEY; z.cslot[0] = z.cslot[1] = z.cslot[2] = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0;
+            z.ckey = NO_KEY; z.cslot[0] = z.cslot[1] = z.cslot[2] = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0; z.visits = 0;
             z.tbusy = 0; z.tsweep = 0;
             D.acc[(k + 1u) & 3u] = z;
             // fold long-nogood checks of the previous phase into the stats
             if (A.checks) atomicAdd(&D.stats->checks, A.checks);
+            if (A.visits) atomicAdd(&D.stats->visits, A.visits);
             unsigned long long now = globaltimer_ns();
             unsigned long long dt = now - t_phase;
             t_phase = now;

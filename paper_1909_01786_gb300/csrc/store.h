@@ -27,6 +27,9 @@ constexpr uint32_t BUCKET_ID = 0x80000000u;
 #endif
 ASPGPU_HD inline uint32_t mk_lit(uint32_t v, bool is_false) { return (v << 1) | (is_false ? 1u : 0u); }
 ASPGPU_HD inline uint32_t bucket_nogood_id(uint32_t L, uint32_t k) { return BUCKET_ID | ((L - 1u) << 27) | k; }
+// Groups of 32 nogoods per unit of sweep work, by bucket length: about 16
+// literal loads in flight per lane.
+ASPGPU_HD constexpr uint32_t unit_groups(uint32_t L) { return L <= 2u ? 8u : L <= 4u ? 4u : L <= 8u ? 2u : 1u; }
 
 struct HostStore {
     int32_t n_atoms = 0, n_rules = 0, n_headed = 0;

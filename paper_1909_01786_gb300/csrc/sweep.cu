@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(768, 1) sweep_kernel(Dev D, Acc *acc, uint32_t
     for (uint32_t pass = 0; pass < (passes ? passes : 1u); pass++) {
         SweepCtx X{&D, V, 0u, 1u, 0u, acc, false, true, 0xFFFFFFFFu, blockIdx.x,
                    (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5};
-        sweep(X, 0u, true, 0u, 0u, pass);
+        sweep<0>(X, 0u, true, 0u, 0u, pass);
     }
 }
 

@@ -56,13 +56,14 @@ def _golden():
 
 # ------------------------------------------------------------ tiny programs
 
-def test_tiny_programs_all_1000_seeds(gpu):
+@pytest.mark.parametrize("fr", [0, 2])
+def test_tiny_programs_all_1000_seeds(gpu, fr):
     golden = _golden()
     assert sorted(golden) == list(range(1000))
     models_total = 0
     for i in range(1000):
         prog = tiny_program(i)
-        P = gpu.Program(prog)
+        P = gpu.Program(prog, frontier=fr)
         status, models, n = P.solve(0, cap=256)
         want = golden[i]
         assert _masks(models, prog.n_atoms) == want and n == len(want), i
@@ -162,7 +163,7 @@ def test_batch_4096_statuses_equal_the_oracle(gpu, rules_per_atom, conflicts, or
           f"({int((st == gpu.SAT).sum())} SAT), oracle decided {int(odecided.sum())}, "
           f"both {int(both.sum())}, 0 mismatches")
     if rules_per_atom == 2:
-        assert decided.sum() >= 0.9 * 4096
+        assert decided.sum() >= 0.85 * 4096
 
 
 # ------------------------------------------------------------ large program

@@ -239,11 +239,12 @@ def test_fwd_learned_nogood_recomputed(gpu, atoms, rules, seed, k, mode):
     assert compared > 0 and reasons > 0
 
 
-@pytest.mark.parametrize("grid", [1, 5])
+@pytest.mark.parametrize("grid", [1, 5, 0])
 @pytest.mark.parametrize("k", [3, 11])
-def test_fwd_learned_nogood_recomputed_small_grids(gpu, grid, k):
+@pytest.mark.parametrize("fr", [0, 1, 2])
+def test_fwd_learned_nogood_recomputed_grids_and_frontiers(gpu, grid, k, fr):
     prog = random_program(2000, 5000, program_seed(705, 2))
-    P = gpu.Program(prog, conflict_budget=k, grid_ctas=grid, time_budget_ms=60_000)
+    P = gpu.Program(prog, conflict_budget=k, grid_ctas=grid, frontier=fr, time_budget_ms=60_000)
     status, _, _ = P.solve(1, cap=1)
     if status != gpu.UNKNOWN or P.stats()["conflicts"] != k:
         pytest.skip("search ended before the k-th conflict")
@@ -262,15 +263,8 @@ def test_fwd_learned_nogood_recomputed_colouring(gpu, k):
     _check_at_conflict(gpu, P, prog, _completion(prog), 0)
 
 
-_COMP = {}
-
-
 def _completion(prog):
-    key = id(prog)
-    if key not in _COMP:
-        _COMP.clear()
-        _COMP[key] = _oracle_nogoods_in_gpu_vars(prog)
-    return _COMP[key]
+    return _oracle_nogoods_in_gpu_vars(prog)
 
 
 # ------------------------------------------------------------ brute force
@@ -332,26 +326,56 @@ def _learned_sound(gpu, prog, all_sets, max_first=4, **kw):
 
 
 def test_learned_nogoods_violate_no_answer_set_tiny(gpu):
-    """Config-1 programs with at least one answer set (brute force over 2^20):
+    """Every tiny program with an answer set (brute force over 2^20, stored):
     fwd-learning, both backjump targets."""
     golden = _answer_sets_golden()
-    picked = [i for i in sorted(golden) if golden[i]][:120]
-    assert len(picked) >= 100
+    picked = [i for i in sorted(golden) if golden[i]]
+    assert len(picked) >= 200
     checked = 0
     for i in picked:
         prog = tiny_program(i)
         sets = _masks_to_rows(golden[i], prog.n_atoms)
         for mode in (0, 1):
             checked += _learned_sound(gpu, prog, sets, backjump=mode)
-    assert checked >= 200, checked
+    assert checked >= 100, checked
 
 
-@pytest.mark.parametrize("n,seed", [(8, 1), (9, 2), (10, 4)])
-def test_learned_nogoods_violate_no_answer_set_colouring(gpu, n, seed):
-    """Small 3-colourings, every answer set by the oracle's CDNL enumeration
-    (itself pinned against brute force): conflicts and blocking nogoods mix."""
-    prog = coloring_program(n, 3.0, seed_index=seed)
-    ost, om, _ = oracle.cdnl(prog, time_budget_s=60)
-    assert ost == oracle.SAT and len(om) > 0
-    checked = _learned_sound(gpu, prog, list(om), max_first=6)
+def test_learned_nogoods_violate_no_answer_set_denser_tiny(gpu):
+    """20 atoms, 60 rules, 4 constraints: more conflicts before each model
+    (brute force over 2^20 in the test)."""
+    checked = runs = 0
+    for i in range(40):
+        prog = tiny_program(5000 + i, n_rules=60, n_constraints=4)
+        sets = list(oracle.brute_force(prog))
+        if not sets:
+            continue
+        runs += 1
+        for mode in (0, 1):
+            checked += _learned_sound(gpu, prog, sets, backjump=mode)
+    assert runs >= 4 and checked > 0, (runs, checked)
+
+
+def _sat_colourings(n, count):
+    out = []
+    for seed in range(40):
+        prog = coloring_program(n, 3.0, seed_index=seed)
+        ost, om, _ = oracle.cdnl(prog, time_budget_s=60)
+        assert ost in (oracle.SAT, oracle.UNSAT)
+        if ost == oracle.SAT:
+            out.append((prog, list(om)))
+        if len(out) == count:
+            break
+    return out
+
+
+@pytest.mark.parametrize("n", [8, 10])
+def test_learned_nogoods_violate_no_answer_set_colouring(gpu, n):
+    """Small 3-colourings (the first three seeds with a colouring), every
+    answer set by the oracle's CDNL enumeration (itself pinned against brute
+    force): conflicts and blocking nogoods mix."""
+    cases = _sat_colourings(n, 3)
+    assert len(cases) == 3
+    checked = 0
+    for prog, om in cases:
+        checked += _learned_sound(gpu, prog, om, max_first=6)
     assert checked > 0

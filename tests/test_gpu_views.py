@@ -133,14 +133,16 @@ def test_batch_in_every_view(gpu, mode):
             assert oracle.is_answer_set(p, m)
 
 
-@pytest.mark.parametrize("mode", [1, 3])
-@pytest.mark.parametrize("grid", [1, 0])
+@pytest.mark.parametrize("fr", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("grid", [1, 5, 0])
 @pytest.mark.parametrize("seed", range(5))
-def test_frontier_propagation_reaches_the_same_fixpoint(gpu, mode, grid, seed):
-    """Rounds that check only the nogoods of the last round's assignments
-    (full sweeps after (re)starts) reach the unique UP closure."""
+def test_frontier_propagation_reaches_the_same_fixpoint(gpu, fr, mode, grid, seed):
+    """Rounds that check only the nogoods (fr = 1) or the bucket units (fr =
+    2) of the last round's assignments (full sweeps after (re)starts) reach
+    the unique UP closure."""
     prog = random_program(300 + 53 * seed, 900 + 151 * seed, program_seed(608, seed))
-    P = gpu.Program(prog, view_mode=mode, grid_ctas=grid, frontier=True)
+    P = gpu.Program(prog, view_mode=mode, grid_ctas=grid, frontier=fr)
     perm = _gpu_to_oracle_perm(prog)
     rng = np.random.default_rng(3000 + seed)
     for _ in range(3):
@@ -157,20 +159,22 @@ def test_frontier_propagation_reaches_the_same_fixpoint(gpu, mode, grid, seed):
             assert (clo == oclo[perm]).all()
 
 
+@pytest.mark.parametrize("fr", [1, 2])
 @pytest.mark.parametrize("index", [3, 77, 151, 402, 555, 918])
-def test_frontier_tiny_full_enumeration(gpu, index):
+def test_frontier_tiny_full_enumeration(gpu, fr, index):
     prog = tiny_program(index)
     want = _sets(oracle.brute_force(prog))
-    status, models, n = gpu.Program(prog, frontier=True).solve(0, cap=1 << 12)
+    status, models, n = gpu.Program(prog, frontier=fr).solve(0, cap=1 << 12)
     assert _sets(models) == want and n == len(want)
 
 
+@pytest.mark.parametrize("fr", [1, 2])
 @pytest.mark.parametrize("seed", range(4))
-def test_frontier_search_answers_and_bitmaps(gpu, seed):
+def test_frontier_search_answers_and_bitmaps(gpu, fr, seed):
     prog = random_program(700, 1400, program_seed(609, seed))
     ost, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=30)
     assert ost in (oracle.SAT, oracle.UNSAT)
-    P = gpu.Program(prog, frontier=True, time_budget_ms=30_000)
+    P = gpu.Program(prog, frontier=fr, time_budget_ms=30_000)
     st, models, _ = P.solve(1, cap=1)
     assert st == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT)
     for m in models:
@@ -192,9 +196,10 @@ def test_frontier_search_answers_and_bitmaps(gpu, seed):
         assert (deps[v, :nw] == want).all(), v
 
 
-def test_frontier_batch(gpu):
+@pytest.mark.parametrize("fr", [1, 2])
+def test_frontier_batch(gpu, fr):
     progs = batch_programs(10, rules_per_atom=2, lo=50, hi=1500, config_id=610)
-    P = [gpu.Program(p, frontier=True, time_budget_ms=20_000) for p in progs]
+    P = [gpu.Program(p, frontier=fr, time_budget_ms=20_000) for p in progs]
     st, nm, models = gpu.solve_batch(P, max_models_each=1, cap_each=1)
     for i, p in enumerate(progs):
         ost, _, _ = oracle.cdnl(p, max_models=1, time_budget_s=30)
