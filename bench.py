@@ -67,6 +67,10 @@ def _args():
                     help="atoms of the store-larger-than-L2 program (4 rules per atom); 0 = skip that leg")
     ap.add_argument("--big-conflicts", type=int, default=40, help="conflict budget of the in-solver leg on it")
     ap.add_argument("--tiny", type=int, default=1000, help="tiny programs enumerated (config-1 family); 0 = skip")
+    ap.add_argument("--batch-ms", type=int, default=2000,
+                    help="device time budget per program of the batched leg (the oracle gets the same in CPU time)")
+    ap.add_argument("--batch-frontier", type=int, default=2,
+                    help="propagation rounds of the batched leg (0 full sweeps, 2 the unit frontier)")
     ap.add_argument("--batch-rules-per-atom", type=int, default=2,
                     help="rules per atom of the batched workload (2: the family decides within the budget)")
     ap.add_argument("--sweep-only", type=int, default=0,
@@ -426,9 +430,12 @@ def _frontiers(a, aspgpu, prog):
     lists), and the unit frontier (dirty bucket units).  Device time, rates,
     rounds per decision, and literals and nogoods checked per round."""
     out = {}
-    for name, fr in (("full", aspgpu.FRONTIER_FULL), ("nogoods", aspgpu.FRONTIER_NOGOODS),
-                     ("units", aspgpu.FRONTIER_UNITS)):
-        P = aspgpu.Program(prog, frontier=fr, conflict_budget=a.conflicts, time_budget_ms=60_000, view_mode=a.view)
+    for name, fr, grid in (("full", aspgpu.FRONTIER_FULL, 0), ("nogoods", aspgpu.FRONTIER_NOGOODS, 0),
+                           ("units", aspgpu.FRONTIER_UNITS, 0), ("units_chained", aspgpu.FRONTIER_UNITS_CHAINED, 0),
+                           ("units_76_ctas", aspgpu.FRONTIER_UNITS, 76), ("units_38_ctas", aspgpu.FRONTIER_UNITS, 38),
+                           ("units_chained_76_ctas", aspgpu.FRONTIER_UNITS_CHAINED, 76)):
+        P = aspgpu.Program(prog, frontier=fr, conflict_budget=a.conflicts, time_budget_ms=60_000, view_mode=a.view,
+                           grid_ctas=grid)
         P.solve(1, cap=1)                          # warm-up solve
         status, _, _ = P.solve(1, cap=1)
         s = P.stats()
@@ -441,7 +448,9 @@ def _frontiers(a, aspgpu, prog):
                      "us_per_round": s["ns_total"] / rounds / 1e3,
                      "literal_checks_per_round": s["literal_checks"] / rounds,
                      "nogood_visits_per_round": s["nogood_visits"] / rounds,
-                     "literal_checks_per_s": s["literal_checks"] / sec}
+                     "literal_checks_per_s": s["literal_checks"] / sec,
+                     "us_per_round_split": {k: s[k] / rounds / 1e3 for k in (
+                         "ns_slowest_cta", "ns_slowest_sweep", "ns_buckets", "ns_learned", "ns_barrier")}}
         P.close()
     full = out["full"]["decisions_per_s"]
     for v in out.values():
@@ -489,8 +498,8 @@ def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
     lo, hi = shard_bounds(a.batch, rank, world)
     rpa = a.batch_rules_per_atom
     progs = batch_programs(hi - lo, rules_per_atom=rpa, config_id=4, first_index=lo) if hi > lo else []
-    kw = dict(conflict_budget=a.batch_conflicts, time_budget_ms=20_000, deps_levels=1024,
-              learned_capacity=1 << 20)
+    kw = dict(conflict_budget=a.batch_conflicts, time_budget_ms=a.batch_ms, deps_levels=1024,
+              learned_capacity=1 << 20, frontier=a.batch_frontier)
     P = [aspgpu.Program(p, **kw) for p in progs]
     solved_b = solved_p = agree = 0
     tb = tp = t_prepare = 0.0
@@ -525,14 +534,14 @@ def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
             q.close()
     oracle_part = None
     if rank == 0 and progs:
-        ost, osec, owall, cores = _oracle_pool(progs, 2.0)
+        ost, osec, owall, cores = _oracle_pool(progs, a.batch_ms / 1e3)
         ost = np.array(ost)
         od = (ost == 10) | (ost == 20)
         gd = (st == 10) | (st == 20)
         both = od & gd
         oracle_part = {"solved": int(od.sum()), "seconds": owall, "cores": cores,
                        "solved_per_s": int(od.sum()) / owall if owall else None,
-                       "budget": "2 s of CPU per program", "decided_by_both": int(both.sum()),
+                       "budget": f"{a.batch_ms / 1e3:g} s of CPU per program", "decided_by_both": int(both.sum()),
                        "status_mismatches": int((ost[both] != st[both]).sum())}
     if world > 1:
         # whole-job figures: MAX of the times, SUM of the counts
@@ -542,7 +551,8 @@ def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
         solved_b, solved_p, agree = int(solved_b), int(solved_p), int(agree)
     pct = (lambda q: float(np.percentile(plain_ms, q)) if plain_ms else None)
     return {"workload": f"{a.batch} programs, {rpa} rules per atom, atoms log-uniform in [200, 20000], "
-                        f"conflict budget {a.batch_conflicts} per program, first answer set"
+                        f"conflict budget {a.batch_conflicts} and {a.batch_ms} ms per program, first answer set, "
+                        f"frontier mode {a.batch_frontier} (batched and plain)"
                         + (f"; {world} ranks, one block of programs each" if world > 1 else ""),
             "batched": {"seconds": tb, "solved": solved_b, "solved_per_s": solved_b / tb if tb else None,
                         "prepare_seconds": t_prepare, "autotune": info},
@@ -679,7 +689,7 @@ def _summary(out):
         "learned_speedup": [g(out, "learned_heuristic", "speedup_solved_per_s"),
                             g(out, "learned_heuristic", "speedup_static_solved_per_s")],
         "frontier_decisions_per_s": {k: g(out, "frontier_compare", k, "decisions_per_s")
-                                     for k in ("full", "nogoods", "units")},
+                                     for k in (out.get("frontier_compare") or {})},
     }
 
 

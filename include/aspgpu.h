@@ -100,6 +100,10 @@ extern "C" {
 #define ASP_FRONTIER_FULL 0
 #define ASP_FRONTIER_NOGOODS 1
 #define ASP_FRONTIER_UNITS 2
+/* UNITS_CHAINED: as UNITS, and inside a round a claim also queues its CTA's
+ * own units that hold the claimed variable, which later waves of the same
+ * sweep check (up to three more waves; single-program solving). */
+#define ASP_FRONTIER_UNITS_CHAINED 3
 
 /* Backjump target of fwd-learning, with h the highest level in the
  * conflict's dependency bitmap.  H_MINUS_1: level h-1 (Algorithm 4's

@@ -21,7 +21,7 @@ HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED, HEUR_LEARNED_STATIC, HEUR_JW = 0, 
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 VIEW_AUTO, VIEW_PLAIN, VIEW_PACKED, VIEW_BYTES = 0, 1, 2, 3
 LEARN_FWD, LEARN_RES = 0, 1
-FRONTIER_FULL, FRONTIER_NOGOODS, FRONTIER_UNITS = 0, 1, 2
+FRONTIER_FULL, FRONTIER_NOGOODS, FRONTIER_UNITS, FRONTIER_UNITS_CHAINED = 0, 1, 2, 3
 BACKJUMP_H_MINUS_1, BACKJUMP_ASSERTING = 0, 1
 R_DECISION, R_COMPLETE, R_INPUT = 0xFFFFFFFF, 0xFFFFFFFE, 0xFFFFFFFD
 

@@ -13,7 +13,13 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libaspgpu.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["solve.cu", "batch.cu", "sweep.cu", "noalloc.cu", "mlp.cu", "api.cpp", "store.cpp"]
+# (source, extra flags, object name): batch_kernel.cu is compiled once per
+# batch configuration and frontier mode, so the four instantiations of the
+# batch kernel compile in parallel
+SOURCES = [("solve.cu", [], "solve"), ("solve_units.cu", [], "solve_units"), ("batch.cu", [], "batch")]
+SOURCES += [("batch_kernel.cu", [f"-DBATCH_CONFIG={c}", f"-DBATCH_UNITS={u}"], f"batch_kernel_c{c}_u{u}")
+            for c in (0, 1) for u in (0, 1)]
+SOURCES += [(f, [], f.split(".")[0]) for f in ("sweep.cu", "noalloc.cu", "mlp.cu", "api.cpp", "store.cpp")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,16 +45,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
     jobs = []
     objs = []
-    for src in SOURCES:
+    for src, flags, name in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(OUT_DIR, src + ".o")
+        obj = os.path.join(OUT_DIR, name + ".o")
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
-            cmd = [nvcc] + ARCH + common + ["-lineinfo", "-c", path, "-o", obj]
-            if src.endswith(".cu"):
-                cmd += ["-Xptxas", "-v"] if verbose else []
-            else:
-                cmd += ["-x", "cu"] if False else []
+            cmd = [nvcc] + ARCH + common + flags + ["-lineinfo", "-c", path, "-o", obj]
+            if src.endswith(".cu") and verbose:
+                cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:

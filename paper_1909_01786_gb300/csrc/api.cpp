@@ -20,8 +20,8 @@ cudaError_t launch_sweep(const Dev &D, Acc *acc, int grid, int block, size_t sme
                          uint32_t passes);
 int batch_threads(int config);
 int mlp_prior(const uint16_t *d_w, const std::vector<float> &features, int64_t n, float *d_out, cudaStream_t st);
-cudaError_t batch_configure(int config, size_t smem, int *blocks_per_sm);
-cudaError_t launch_batch(int config, const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
+cudaError_t batch_configure(int config, bool units, size_t smem, int *blocks_per_sm);
+cudaError_t launch_batch(int config, bool units, const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, int grid,
                          size_t smem, cudaStream_t st);
 }  // namespace aspgpu
 
@@ -272,9 +272,11 @@ static int unit_lists(asp_prog *p, const HostStore &H, const std::vector<uint32_
     return ASP_OK;
 }
 
+// (a partition without lists sweeps everything; one with lists keeps the
+// requested unit mode, 2 or 3)
 static void use_unit_lists(Dev &D, const UnitLists &U)
 {
-    D.frontier = U.built ? 2u : 0u;
+    D.frontier = U.built ? (D.frontier >= 2u ? D.frontier : 2u) : 0u;
     D.cta_ubase = U.ubase;
     D.occ_uoff = U.uoff;
     D.occ_unit = U.unit;
@@ -338,7 +340,7 @@ static int plan_grid(asp_prog *p, const HostStore &H)
     int rc = choose_view(p, H, D, boff, alo, an, base_smem, max_smem);
     if (rc != ASP_OK) return rc;
     p->smem = base_smem + 4 * D.view_words;
-    if (D.frontier == 2) {
+    if (D.frontier >= 2) {
         UnitLists U;
         rc = unit_lists(p, H, boff, D.G, ~0ull, U);
         if (rc != ASP_OK) return rc;
@@ -377,12 +379,15 @@ static int plan_batch(asp_prog *p, const HostStore &H, int config)
     D1.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D1.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D1.cta_auxn = upload(p, an, rc);
-    if (rc == ASP_OK && p->D.frontier == 2) {
+    if (rc == ASP_OK && p->D.frontier >= 2) {
         // one program per CTA: the units of the whole store (the same for
         // both configurations); programs too large for batches keep full
         // sweeps there
         if (config == 0) rc = unit_lists(p, H, boff, 1u, BATCH_MAX_UNITS, p->batch_units);
-        if (rc == ASP_OK) use_unit_lists(D1, p->batch_units);
+        if (rc == ASP_OK) {
+            use_unit_lists(D1, p->batch_units);
+            D1.frontier = p->batch_units.built ? 2u : 0u;    // no chaining in batches
+        }
     }
     p->D1[config] = D1;
     p->smem1[config] = base + 4 * D1.view_words;
@@ -397,6 +402,7 @@ struct asp_batch {
     std::vector<int64_t> caps;
     int64_t max_models_each = 0;
     int config = 0, grid = 0;
+    bool units = false;                 // some program sweeps by the frontier by units
     size_t smem = 0;
     double trial_ns[2] = {0.0, 0.0};
     uint32_t queued = 0;
@@ -448,7 +454,7 @@ int batch_prepare(asp_batch *b, int config, const std::vector<uint32_t> &order, 
     size_t smem = 0;
     for (asp_prog *p : b->progs) smem = std::max(smem, p->smem1[config]);
     int per_sm = 0;
-    cudaError_t e = batch_configure(config, smem, &per_sm);
+    cudaError_t e = batch_configure(config, b->units, smem, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "batch configuration");
     if (per_sm < 1) return fail(ASP_E_CUDA, "batch kernel cannot be resident");
     const std::vector<Dev> devs = batch_descriptors(b, config, trial);
@@ -473,7 +479,7 @@ cudaError_t batch_enqueue(asp_batch *b)
     uint32_t *d_order = (uint32_t *)((char *)b->scratch + sizeof(Dev) * n);
     unsigned int *d_queue = (unsigned int *)((char *)d_order + 4 * n);
     cudaError_t e = cudaMemsetAsync(d_queue, 0, 64, b->stream);
-    if (e == cudaSuccess) e = launch_batch(b->config, d_devs, d_order, b->queued, d_queue, b->grid, b->smem, b->stream);
+    if (e == cudaSuccess) e = launch_batch(b->config, b->units, d_devs, d_order, b->queued, d_queue, b->grid, b->smem, b->stream);
     return e;
 }
 
@@ -589,7 +595,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
         return fail(ASP_E_ARG, "conflicts_per_round must be 0..4");
     }
     D.conf_per_round = (uint32_t)std::max(1, p->opt.conflicts_per_round);
-    if (p->opt.frontier < 0 || p->opt.frontier > 2) { delete p; return fail(ASP_E_ARG, "unknown frontier mode"); }
+    if (p->opt.frontier < 0 || p->opt.frontier > 3) { delete p; return fail(ASP_E_ARG, "unknown frontier mode"); }
     D.frontier = (uint32_t)p->opt.frontier;
     D.stall_cta = 0xFFFFFFFFu;
     D.barrier_ns = 20000000000ull;
@@ -658,6 +664,14 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
         return q;
     };
     D.learned_ids = (uint32_t *)alloc((size_t)D.learned_ng_cap * 4);
+    D.nwatch = (uint2 *)alloc(((size_t)D.n_long + D.learned_ng_cap) * sizeof(uint2));
+    if (rc == ASP_OK && D.n_long > 0) {
+        // long static nogoods (more than BUCKET_MAX literals) watch their first two
+        std::vector<uint2> w0(D.n_long, make_uint2(0u, 1u));
+        cudaError_t e = cudaMemcpyAsync(D.nwatch, w0.data(), w0.size() * sizeof(uint2), cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "watches");
+    }
     D.act = (uint32_t *)alloc((size_t)D.J * 4 + 4);
     D.asg = (uint32_t *)alloc((size_t)D.asg_words * 4 + 4);
     D.dl = (int32_t *)alloc((size_t)D.nv * 4 + 4);
@@ -1122,6 +1136,7 @@ int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each,
     b->max_models_each = max_models_each;
     b->caps.resize(n);
     for (int32_t i = 0; i < n; i++) b->caps[i] = models_cap ? models_cap[i] : 0;
+    for (int32_t i = 0; i < n; i++) b->units |= progs[i]->D1[0].frontier == 2u;
     auto bail = [&](int rc) { asp_batch_free(b); return rc; };
     // model buffers of every program
     for (int32_t i = 0; i < n; i++) {

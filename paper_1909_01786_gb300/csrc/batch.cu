@@ -1,56 +1,11 @@
-// Batched solving: many programs in one launch, one CTA per program
-// (device code in solver.cuh).
-#include "solver.cuh"
+// Batched solving: many programs in one launch, one CTA per program.  The
+// kernel (kernels.cuh) is compiled once per configuration and frontier mode
+// in batch_kernel.cu; this unit dispatches to those instantiations.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
 
 namespace aspgpu {
-
-// Batched solving: each CTA takes programs from a queue (the host orders it
-// largest first) and solves each alone, with the whole program's assignment
-// view in its shared memory and a CTA barrier as the phase barrier.
-template <int THREADS, int MIN_BLOCKS>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *devs, const uint32_t *order, uint32_t n,
-                                                                    unsigned int *queue)
-{
-    extern __shared__ unsigned long long smem_raw[];
-    __shared__ Dev sD;
-    __shared__ uint32_t s_item;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            uint32_t i = atomicAdd(queue, 1u);
-            s_item = i < n ? __ldg(order + i) : 0xFFFFFFFFu;
-            if (s_item != 0xFFFFFFFFu) sD = devs[s_item];
-        }
-        cta_sync();
-        if (s_item == 0xFFFFFFFFu) break;
-        const Dev &D = sD;
-        // reset this program's search state
-        for (uint32_t w = threadIdx.x; w <= D.asg_words; w += blockDim.x) D.asg[w] = 0u;
-        for (uint32_t v = threadIdx.x; v < D.nv; v += blockDim.x) D.dl[v] = 0;
-        for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) D.act[j] = 0u;
-        if (D.frontier == 2u)
-            for (uint32_t w = threadIdx.x; w < 2u * D.dirty_words; w += blockDim.x) D.dirty[w] = 0u;
-        if (threadIdx.x == 0) {
-            Ctl c;
-            memset(&c, 0, sizeof(c));
-            c.op = OP_INIT;
-            c.cdl = 1;
-            c.lfill = D.lits_static;
-            D.ctl[0] = c;
-            memset(&c, 0, sizeof(c));
-            D.ctl[1] = c;
-            Acc a;
-            a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.visits = 0; a.tbusy = 0; a.tsweep = 0;
-            for (int i = 0; i < 4; i++) D.acc[i] = a;
-            memset(D.stats, 0, sizeof(DevStats));
-            memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check
-        }
-        cta_sync();
-        const Smem S = make_smem(D, smem_raw);
-        const View V = make_view(D, S.misc + 16, 0);
-        solver_loop<true>(D, S, V, threadIdx.x, blockDim.x, true, threadIdx.x == 0, 0);
-        cta_sync();
-    }
-}
 
 // Batch kernel configurations the autotuner chooses from: threads per CTA
 // and the CTAs per SM the register budget is compiled for.
@@ -58,24 +13,32 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *d
 //   1: 128 threads, 6 per SM (twice the programs in flight, ~34 KB views)
 int batch_threads(int config) { return config == 1 ? 128 : 256; }
 
-cudaError_t batch_configure(int config, size_t smem, int *blocks_per_sm)
+// batch_kernel.cu, compiled with BATCH_CONFIG = c and BATCH_UNITS = u
+#define ASP_BATCH_DECL(c, u)                                                                                  \
+    cudaError_t batch_configure_c##c##_u##u(size_t smem, int *blocks_per_sm);                                   \
+    cudaError_t launch_batch_c##c##_u##u(const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue, \
+                                         int grid, size_t smem, cudaStream_t st);
+ASP_BATCH_DECL(0, 0)
+ASP_BATCH_DECL(0, 1)
+ASP_BATCH_DECL(1, 0)
+ASP_BATCH_DECL(1, 1)
+#undef ASP_BATCH_DECL
+
+// units: the kernels compiled with the frontier by units
+cudaError_t batch_configure(int config, bool units, size_t smem, int *blocks_per_sm)
 {
-    if (config == 1) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<128, 6>, 128, smem);
-    }
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<256, 3>, 256, smem);
+    if (config == 1) return units ? batch_configure_c1_u1(smem, blocks_per_sm) : batch_configure_c1_u0(smem, blocks_per_sm);
+    return units ? batch_configure_c0_u1(smem, blocks_per_sm) : batch_configure_c0_u0(smem, blocks_per_sm);
 }
 
-cudaError_t launch_batch(int config, const Dev *devs, const uint32_t *order, uint32_t n, unsigned int *queue,
-                         int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_batch(int config, bool units, const Dev *devs, const uint32_t *order, uint32_t n,
+                         unsigned int *queue, int grid, size_t smem, cudaStream_t st)
 {
-    if (config == 1) batch_kernel<128, 6><<<grid, 128, smem, st>>>(devs, order, n, queue);
-    else batch_kernel<256, 3><<<grid, 256, smem, st>>>(devs, order, n, queue);
-    return cudaGetLastError();
+    if (config == 1)
+        return units ? launch_batch_c1_u1(devs, order, n, queue, grid, smem, st)
+                     : launch_batch_c1_u0(devs, order, n, queue, grid, smem, st);
+    return units ? launch_batch_c0_u1(devs, order, n, queue, grid, smem, st)
+                 : launch_batch_c0_u0(devs, order, n, queue, grid, smem, st);
 }
 
 }  // namespace aspgpu

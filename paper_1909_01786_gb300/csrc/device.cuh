@@ -149,6 +149,9 @@ struct Dev {
     uint32_t *lits;                      // buckets | long | units | learned
     const uint32_t *long_ids;
     uint32_t *learned_ids;
+    // watched literals of the long and learned nogoods (Algorithm 2): two
+    // positions per nogood, long nogood i at i, learned nogood i at n_long + i
+    uint2 *nwatch;
     const int32_t *rule_head;
     const uint32_t *rpos_off, *rpos, *rneg_off, *rneg, *score;
     uint32_t *act;

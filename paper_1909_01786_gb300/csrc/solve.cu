@@ -1,36 +1,37 @@
-// The single-program solver: one persistent cooperative kernel over the
-// whole grid runs Algorithm 1 (device code in solver.cuh).
-#include "solver.cuh"
+// The single-program solver without the frontier by units (kernel in
+// kernels.cuh), and the dispatch to solve_units.cu.
+#include "kernels.cuh"
 
 namespace aspgpu {
 
-__global__ void __launch_bounds__(768, 1) solve_kernel(Dev D)
-{
-    extern __shared__ unsigned long long smem_raw[];
-    const Smem S = make_smem(D, smem_raw);
-    const View V = make_view(D, S.misc + 16, blockIdx.x);
-    solver_loop<false>(D, S, V, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, blockIdx.x == 0,
-                       blockIdx.x == 0 && threadIdx.x == 0, blockIdx.x);
-}
-
 cudaError_t sweep_configure();
 
+cudaError_t solve_units_configure(int block, size_t smem, int *blocks_per_sm);
+cudaError_t launch_solve_units(const Dev &D, int grid, int block, size_t smem, cudaStream_t st);
+
+// Both solve kernels (without and with the frontier by units): the CTAs per
+// SM the smaller of the two allows.
 cudaError_t solve_configure(int block, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
     e = sweep_configure();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, block, smem);
+    int a = 0, b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, solve_kernel<false>, block, smem);
+    if (e == cudaSuccess) e = solve_units_configure(block, smem, &b);
+    *blocks_per_sm = a < b ? a : b;
+    return e;
 }
 
-cudaError_t solve_attributes(cudaFuncAttributes *a) { return cudaFuncGetAttributes(a, solve_kernel); }
+cudaError_t solve_attributes(cudaFuncAttributes *a) { return cudaFuncGetAttributes(a, solve_kernel<false>); }
 
 cudaError_t launch_solve(const Dev &D, int grid, int block, size_t smem, cudaStream_t st)
 {
+    if (D.frontier >= 2u) return launch_solve_units(D, grid, block, smem, st);
     Dev copy = D;
     void *args[] = {(void *)&copy};
-    return cudaLaunchCooperativeKernel((void *)solve_kernel, dim3(grid), dim3(block), args, smem, st);
+    return cudaLaunchCooperativeKernel((void *)solve_kernel<false>, dim3(grid), dim3(block), args, smem, st);
 }
 
 }  // namespace aspgpu

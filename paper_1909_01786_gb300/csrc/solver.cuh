@@ -329,6 +329,10 @@ struct SweepCtx {
     bool listed = false;
     // frontier by units: the next round's dirty bitmap (null otherwise)
     uint32_t *dmark = nullptr;
+    // frontier by units with chaining in the round (frontier = 3): a claim
+    // queues the CTA's own units that hold its variable for a later wave of
+    // the same sweep
+    bool chain = false;
 };
 
 constexpr uint32_t CLAIM_BUF = 256;
@@ -350,6 +354,50 @@ __shared__ unsigned long long s_tlearned, s_tbuckets;
 constexpr uint32_t DQ_CAP = 1024;
 __shared__ uint32_t s_dq[DQ_CAP];
 __shared__ unsigned int s_nq;
+// frontier = 3: units already in this round's queue (local units below
+// DQ_BITS), the per-wave pop counters, and the CTA's global unit range
+constexpr uint32_t DQ_BITS = 4096, DQ_WAVES = 4;
+__shared__ uint32_t s_dqbits[DQ_BITS / 32];
+__shared__ unsigned int s_wave[DQ_WAVES];
+__shared__ uint32_t s_ub[3];
+
+// Queue local unit `local` once per round (frontier = 3); the caller keeps
+// it below DQ_BITS.
+__device__ __forceinline__ void dq_push_once(uint32_t local)
+{
+    const uint32_t bit = 1u << (local & 31u);
+    if (atomicOr(&s_dqbits[local >> 5], bit) & bit) return;
+    const uint32_t pos = atomicAdd(&s_nq, 1u);
+    if (pos < DQ_CAP) s_dq[pos] = local;
+}
+
+// frontier = 3: after a claim of x is published in the CTA's view, queue
+// the CTA's own units that hold x for the next wave of this sweep (units of
+// other CTAs, and any that do not fit, are checked next round through the
+// dirty bitmap).  All 32 lanes call it with the same x.
+__device__ __forceinline__ void warp_push_units(const SweepCtx &X, uint32_t x)
+{
+    const Dev &D = *X.D;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t ub0 = s_ub[0], ub1 = s_ub[1];
+    const uint32_t o0 = __ldg(D.occ_uoff + x), o1 = __ldg(D.occ_uoff + x + 1u);
+    for (uint32_t o = o0 + lane; o < o1; o += 32u) {
+        const uint32_t u = __ldg(D.occ_unit + o);
+        if (u >= ub0 && u < ub1 && u - ub0 < DQ_BITS) dq_push_once(u - ub0);
+    }
+}
+
+// The same from one lane.
+__device__ __forceinline__ void lane_push_units(const SweepCtx &X, uint32_t x)
+{
+    const Dev &D = *X.D;
+    const uint32_t ub0 = s_ub[0], ub1 = s_ub[1];
+    const uint32_t o0 = __ldg(D.occ_uoff + x), o1 = __ldg(D.occ_uoff + x + 1u);
+    for (uint32_t o = o0; o < o1; o++) {
+        const uint32_t u = __ldg(D.occ_unit + o);
+        if (u >= ub0 && u < ub1 && u - ub0 < DQ_BITS) dq_push_once(u - ub0);
+    }
+}
 
 // Frontier by units: this CTA's bucket units to check in the round -- those
 // whose bit is set in the round's dirty bitmap `buf` (set by the claims of
@@ -377,8 +425,13 @@ __device__ __forceinline__ void build_unit_queue(const Dev &D, uint32_t cta, uin
             while (bits) {
                 const uint32_t b = (uint32_t)__ffs(bits) - 1u;
                 bits &= bits - 1u;
-                const uint32_t pos = atomicAdd(&s_nq, 1u);
-                if (pos < DQ_CAP) s_dq[pos] = w * 32u + b - ub0;
+                const uint32_t local = w * 32u + b - ub0;
+                if (D.frontier == 3u && local < DQ_BITS) {
+                    dq_push_once(local);
+                } else {
+                    const uint32_t pos = atomicAdd(&s_nq, 1u);
+                    if (pos < DQ_CAP) s_dq[pos] = local;
+                }
             }
         }
     }
@@ -387,8 +440,12 @@ __device__ __forceinline__ void build_unit_queue(const Dev &D, uint32_t cta, uin
         for (uint32_t o = o0 + lane; o < o1; o += 32u) {
             const uint32_t u = __ldg(D.occ_unit + o);
             if (u >= ub0 && u < ub1) {
-                const uint32_t pos = atomicAdd(&s_nq, 1u);
-                if (pos < DQ_CAP) s_dq[pos] = u - ub0;
+                if (D.frontier == 3u && u - ub0 < DQ_BITS) {
+                    dq_push_once(u - ub0);
+                } else {
+                    const uint32_t pos = atomicAdd(&s_nq, 1u);
+                    if (pos < DQ_CAP) s_dq[pos] = u - ub0;
+                }
             }
         }
     }
@@ -537,6 +594,65 @@ __device__ __forceinline__ void warp_deps(const SweepCtx &X, const uint32_t (&va
     }
 }
 
+// Dependency bitmaps (Section 4.2, mk_dl_bitmap) -- and, with the frontier
+// by units, the unit marks -- of every claim of a group of 32 nogoods at
+// once: the claims take equal shares of the warp's lanes (32 / p2 lanes
+// each, p2 the claim count rounded up to a power of two), and the lanes of a
+// claim split its bitmap words and its occurrence list, so the group costs
+// the two dependent loads of one claim whatever the number of claims.  All 32
+// lanes call it; won: this lane's nogood claimed x; tl: its literals as view
+// entries.  Returns whether the group made a claim.
+template <int L, bool MARK>
+__device__ __forceinline__ bool group_claims(const SweepCtx &X, bool won, const uint32_t (&tl)[L], uint32_t x)
+{
+    const Dev &D = *X.D;
+    const unsigned m = __ballot_sync(FULL_MASK, won);
+    if (!m) return false;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nc = (uint32_t)__popc(m);
+    uint32_t p2 = 1u;
+    while (p2 < nc) p2 <<= 1;
+    const uint32_t gs = 32u / p2, c = lane / gs, sub = lane % gs;
+    // the lane of the c-th claim
+    unsigned mm = m;
+    for (uint32_t i = 0; i < c && mm; i++) mm &= mm - 1u;
+    const int src = mm ? __ffs(mm) - 1 : 0;
+    uint32_t var[L];
+#pragma unroll
+    for (int q = 0; q < L; q++) var[q] = X.V.var(__shfl_sync(FULL_MASK, tl[q], src) >> 2);
+    const uint32_t xs = __shfl_sync(FULL_MASK, x, src);
+    if (c >= nc) return true;
+    if (X.cdl > 1u) {
+        const uint32_t nw = deps_words(D, X.cdl);
+        const uint32_t dbit = level_bit(D, X.cdl);
+        int32_t Lu[L];
+        bool has_dec = false;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+            const uint32_t u = var[q];
+            has_dec |= u != xs && u == X.dec_v;
+            Lu[q] = (u != xs && u != X.dec_v) ? __ldcg(D.dl + u) : 0;
+        }
+        for (uint32_t w = sub; w < nw; w += gs) {
+            unsigned long long acc = (has_dec && w == (dbit >> 6)) ? (1ull << (dbit & 63u)) : 0ull;
+#pragma unroll
+            for (int q = 0; q < L; q++)
+                if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= __ldcg(D.deps + (size_t)var[q] * D.WW + w);
+            D.deps[(size_t)xs * D.WW + w] = acc;
+        }
+    }
+    if constexpr (MARK) {
+        if (X.dmark) {
+            const uint32_t o0 = __ldg(D.occ_uoff + xs), o1 = __ldg(D.occ_uoff + xs + 1u);
+            for (uint32_t o = o0 + sub; o < o1; o += gs) {
+                const uint32_t u = __ldg(D.occ_unit + o);
+                atomicOr(X.dmark + (u >> 5), 1u << (u & 31u));
+            }
+        }
+    }
+    return true;
+}
+
 // warp_deps for a nogood of L <= BUCKET_MAX literals known at run time
 // (var[q] for q < L).  All 32 lanes call it with the same arguments.
 __device__ __forceinline__ void warp_deps_dyn(const SweepCtx &X, const uint32_t (&var)[BUCKET_MAX], uint32_t L,
@@ -570,7 +686,7 @@ __device__ __forceinline__ void warp_deps_dyn(const SweepCtx &X, const uint32_t 
 // some literal's complement holds, violated if all hold, unit if exactly one
 // is unassigned and the rest hold (Section 2).  Repeats while a claim of
 // this warp changed the view.
-template <int L, int U>
+template <int L, int U, bool MARK>
 __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uint32_t k1, uint32_t stride)
 {
     const Dev &D = *X.D;
@@ -612,7 +728,7 @@ __device__ __forceinline__ void bucket_tasks(const SweepCtx &X, uint32_t k0, uin
             if (r == 2) { report_conflict(X, id, (uint32_t)L); continue; }
             if (r != 0) continue;
             record_claim(X, x, valbit, id);
-            lane_mark_units(X, x);
+            if constexpr (MARK) lane_mark_units(X, x);
             if (X.cdl > 1u) {
                 uint32_t var[L];
 #pragma unroll
@@ -650,7 +766,7 @@ __device__ __forceinline__ uint32_t tlit_count(const View &V, uint32_t tl)
 // and BYTES): every literal is in the view, one shared-memory load and
 // three integer operations classify it.  Lanes past the end of the range
 // load the range's last nogood and drop the result.
-template <int L, int U, bool BYTES>
+template <int L, int U, bool BYTES, bool MARK>
 __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0, uint32_t k1)
 {
     const Dev &D = *X.D;
@@ -705,9 +821,9 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
                     }
                 }
             }
-            if (L > 8 && won) {
+            if (L > 8 && won && (MARK || X.cdl > 1u)) {
                 // long buckets (few claims): the claiming lane alone
-                lane_mark_units(X, x);
+                if constexpr (MARK) lane_mark_units(X, x);
                 if (X.cdl > 1u) {
                     uint32_t var[L];
 #pragma unroll
@@ -715,23 +831,9 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
                     lane_deps<L>(X, var, x);
                 }
             }
-            if (L <= 8 && (X.cdl > 1u || X.dmark)) {
-                // bitmaps (and unit marks) of this group's claims, one claim
-                // at a time, by the warp
-                unsigned m = __ballot_sync(FULL_MASK, won);
-                if (m) {
-                    while (m) {
-                        const int src = __ffs(m) - 1;
-                        m &= m - 1u;
-                        const uint32_t xs = __shfl_sync(FULL_MASK, x, src);
-                        warp_mark_units(X, xs);
-                        if (X.cdl > 1u) {
-                            uint32_t var[L];
-#pragma unroll
-                            for (int q = 0; q < L; q++) var[q] = X.V.var(__shfl_sync(FULL_MASK, lit[t][q], src) >> 2);
-                            warp_deps<L>(X, var, xs);
-                        }
-                    }
+            if (L <= 8 && (X.cdl > 1u || (MARK && X.dmark))) {
+                // bitmaps (and unit marks) of this group's claims, all at once
+                if (group_claims<L, MARK>(X, won, lit[t], x)) {
                     __threadfence_block();
                     __syncwarp();
                 }
@@ -741,50 +843,67 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
                 X.V.put(e, valbit);
                 pub = true;
             }
+            if constexpr (MARK) {
+                if (X.chain) {
+                    // frontier = 3: the CTA's units that hold the claims, for
+                    // the next wave (after the claims are in the view)
+                    if (L > 8) {
+                        if (won) lane_push_units(X, x);
+                    } else {
+                        unsigned m = __ballot_sync(FULL_MASK, won);
+                        while (m) {
+                            const int src = __ffs(m) - 1;
+                            m &= m - 1u;
+                            warp_push_units(X, __shfl_sync(FULL_MASK, x, src));
+                        }
+                    }
+                }
+            }
         }
         if (!X.do_claim || !__any_sync(FULL_MASK, pub)) break;
     }
 }
 
 
-template <bool BYTES>
+template <bool BYTES, bool MARK>
 __device__ __forceinline__ void run_unit_view(const SweepCtx &X, uint32_t L, uint32_t k0, uint32_t k1)
 {
     switch (L) {
-    case 2: bucket_tasks_view<2, unit_groups(2), BYTES>(X, k0, k1); break;
-    case 3: bucket_tasks_view<3, unit_groups(3), BYTES>(X, k0, k1); break;
-    case 4: bucket_tasks_view<4, unit_groups(4), BYTES>(X, k0, k1); break;
-    case 5: bucket_tasks_view<5, unit_groups(5), BYTES>(X, k0, k1); break;
-    case 6: bucket_tasks_view<6, unit_groups(6), BYTES>(X, k0, k1); break;
-    case 7: bucket_tasks_view<7, unit_groups(7), BYTES>(X, k0, k1); break;
-    case 8: bucket_tasks_view<8, unit_groups(8), BYTES>(X, k0, k1); break;
-    case 9: bucket_tasks_view<9, unit_groups(9), BYTES>(X, k0, k1); break;
-    case 10: bucket_tasks_view<10, unit_groups(10), BYTES>(X, k0, k1); break;
-    case 11: bucket_tasks_view<11, unit_groups(11), BYTES>(X, k0, k1); break;
-    case 12: bucket_tasks_view<12, unit_groups(12), BYTES>(X, k0, k1); break;
-    case 13: bucket_tasks_view<13, unit_groups(13), BYTES>(X, k0, k1); break;
-    case 14: bucket_tasks_view<14, unit_groups(14), BYTES>(X, k0, k1); break;
-    default: bucket_tasks_view<15, unit_groups(15), BYTES>(X, k0, k1); break;
+    case 2: bucket_tasks_view<2, unit_groups(2), BYTES, MARK>(X, k0, k1); break;
+    case 3: bucket_tasks_view<3, unit_groups(3), BYTES, MARK>(X, k0, k1); break;
+    case 4: bucket_tasks_view<4, unit_groups(4), BYTES, MARK>(X, k0, k1); break;
+    case 5: bucket_tasks_view<5, unit_groups(5), BYTES, MARK>(X, k0, k1); break;
+    case 6: bucket_tasks_view<6, unit_groups(6), BYTES, MARK>(X, k0, k1); break;
+    case 7: bucket_tasks_view<7, unit_groups(7), BYTES, MARK>(X, k0, k1); break;
+    case 8: bucket_tasks_view<8, unit_groups(8), BYTES, MARK>(X, k0, k1); break;
+    case 9: bucket_tasks_view<9, unit_groups(9), BYTES, MARK>(X, k0, k1); break;
+    case 10: bucket_tasks_view<10, unit_groups(10), BYTES, MARK>(X, k0, k1); break;
+    case 11: bucket_tasks_view<11, unit_groups(11), BYTES, MARK>(X, k0, k1); break;
+    case 12: bucket_tasks_view<12, unit_groups(12), BYTES, MARK>(X, k0, k1); break;
+    case 13: bucket_tasks_view<13, unit_groups(13), BYTES, MARK>(X, k0, k1); break;
+    case 14: bucket_tasks_view<14, unit_groups(14), BYTES, MARK>(X, k0, k1); break;
+    default: bucket_tasks_view<15, unit_groups(15), BYTES, MARK>(X, k0, k1); break;
     }
 }
 
+template <bool MARK>
 __device__ __forceinline__ void run_unit(const SweepCtx &X, uint32_t L, uint32_t k0, uint32_t k1)
 {
     switch (L) {
-    case 2: bucket_tasks<2, unit_groups(2)>(X, k0, k1, 32u); break;
-    case 3: bucket_tasks<3, unit_groups(3)>(X, k0, k1, 32u); break;
-    case 4: bucket_tasks<4, unit_groups(4)>(X, k0, k1, 32u); break;
-    case 5: bucket_tasks<5, unit_groups(5)>(X, k0, k1, 32u); break;
-    case 6: bucket_tasks<6, unit_groups(6)>(X, k0, k1, 32u); break;
-    case 7: bucket_tasks<7, unit_groups(7)>(X, k0, k1, 32u); break;
-    case 8: bucket_tasks<8, unit_groups(8)>(X, k0, k1, 32u); break;
-    case 9: bucket_tasks<9, unit_groups(9)>(X, k0, k1, 32u); break;
-    case 10: bucket_tasks<10, unit_groups(10)>(X, k0, k1, 32u); break;
-    case 11: bucket_tasks<11, unit_groups(11)>(X, k0, k1, 32u); break;
-    case 12: bucket_tasks<12, unit_groups(12)>(X, k0, k1, 32u); break;
-    case 13: bucket_tasks<13, unit_groups(13)>(X, k0, k1, 32u); break;
-    case 14: bucket_tasks<14, unit_groups(14)>(X, k0, k1, 32u); break;
-    default: bucket_tasks<15, unit_groups(15)>(X, k0, k1, 32u); break;
+    case 2: bucket_tasks<2, unit_groups(2), MARK>(X, k0, k1, 32u); break;
+    case 3: bucket_tasks<3, unit_groups(3), MARK>(X, k0, k1, 32u); break;
+    case 4: bucket_tasks<4, unit_groups(4), MARK>(X, k0, k1, 32u); break;
+    case 5: bucket_tasks<5, unit_groups(5), MARK>(X, k0, k1, 32u); break;
+    case 6: bucket_tasks<6, unit_groups(6), MARK>(X, k0, k1, 32u); break;
+    case 7: bucket_tasks<7, unit_groups(7), MARK>(X, k0, k1, 32u); break;
+    case 8: bucket_tasks<8, unit_groups(8), MARK>(X, k0, k1, 32u); break;
+    case 9: bucket_tasks<9, unit_groups(9), MARK>(X, k0, k1, 32u); break;
+    case 10: bucket_tasks<10, unit_groups(10), MARK>(X, k0, k1, 32u); break;
+    case 11: bucket_tasks<11, unit_groups(11), MARK>(X, k0, k1, 32u); break;
+    case 12: bucket_tasks<12, unit_groups(12), MARK>(X, k0, k1, 32u); break;
+    case 13: bucket_tasks<13, unit_groups(13), MARK>(X, k0, k1, 32u); break;
+    case 14: bucket_tasks<14, unit_groups(14), MARK>(X, k0, k1, 32u); break;
+    default: bucket_tasks<15, unit_groups(15), MARK>(X, k0, k1, 32u); break;
     }
 }
 
@@ -792,12 +911,41 @@ __device__ __forceinline__ void run_unit(const SweepCtx &X, uint32_t L, uint32_t
 // stopping once it is satisfied or has two unassigned literals; literals are
 // checked against the global codes, 128 at a time (four loads and their
 // gathers in flight before the first ballot).
-__device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, unsigned long long &checks)
+// Watched literals (Algorithm 2, which uses them for long learned nogoods
+// as well): *wslot holds two positions of the nogood.  If neither watched
+// literal holds -- one's complement is assigned, or both are unassigned --
+// the nogood is neither unit nor violated, and two checks settle it;
+// otherwise the scan runs and moves the watches to literals that do not
+// hold (the complement found, or the first unassigned ones).  Every such
+// nogood is checked every round by one warp, so the watches need no
+// per-variable lists and stay valid across backjumps.  Equal positions
+// (a nogood of one literal) always scan.
+template <bool MARK>
+__device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, unsigned long long &checks,
+                                              uint2 *wslot)
 {
     const Dev &D = *X.D;
     const uint32_t lane = threadIdx.x & 31u;
+    uint2 wp = make_uint2(0u, 0u);
+    if (wslot) {
+        wp = __ldcg(wslot);
+        if (wp.x != wp.y) {
+            // lanes 0 and 1: the two watched literals
+            uint32_t val = 0u, l = 0u;
+            if (lane < 2u) {
+                l = lit_at(D, id + (lane ? wp.y : wp.x)) & ~END_BIT;
+                val = (l >> 1) < D.nv ? global_val(D, l >> 1, X.fresh) : 0u;
+            }
+            const bool opp = lane < 2u && val == ((l & 1u) ? V_T : V_F);
+            const bool un = lane < 2u && val == 0u;
+            const unsigned Bopp = __ballot_sync(FULL_MASK, opp), Bun = __ballot_sync(FULL_MASK, un);
+            checks += 2u;
+            if (Bopp || Bun == 3u) return;
+        }
+    }
     bool any_opp = false, done = false;
     uint32_t n_un = 0, ulit = 0, len = 0;
+    uint32_t opos = 0, upos0 = 0, upos1 = 0;   // positions: a complement found, the first unassigned ones
     for (uint32_t off = id; !done && off < D.lits_cap; off += 128u) {
         uint32_t w[4], code[4];
 #pragma unroll
@@ -810,6 +958,7 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (done) break;
+            const uint32_t pos0 = off - id + 32u * (uint32_t)q;
             unsigned Bend = __ballot_sync(FULL_MASK, (w[q] & END_BIT) != 0u);
             unsigned valid = Bend ? ((2u << (__ffs(Bend) - 1)) - 1u) : FULL_MASK;
             uint32_t l = w[q] & ~END_BIT;
@@ -821,12 +970,31 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
             unsigned Bun = __ballot_sync(FULL_MASK, un);
             uint32_t first_un = __shfl_sync(FULL_MASK, l, Bun ? __ffs(Bun) - 1 : 0);
             if (Bun && n_un == 0) ulit = first_un;
+            if (Bun) {
+                const uint32_t b0 = (uint32_t)__ffs(Bun) - 1u;
+                const unsigned rest = Bun & (Bun - 1u);
+                if (n_un == 0) {
+                    upos0 = pos0 + b0;
+                    if (rest) upos1 = pos0 + (uint32_t)__ffs(rest) - 1u;
+                } else if (n_un == 1) {
+                    upos1 = pos0 + b0;
+                }
+            }
+            if (Bopp) opos = pos0 + (uint32_t)__ffs(Bopp) - 1u;
             n_un += (uint32_t)__popc(Bun);
             len += (uint32_t)__popc(valid);
             checks += (uint32_t)__popc(valid);
             if (Bopp) { any_opp = true; done = true; }
             else if (Bend || n_un > 1) done = true;
         }
+    }
+    if (wslot && lane == 0 && (any_opp || n_un > 0)) {
+        // the watches move to literals that do not hold
+        uint2 nw;
+        if (any_opp) nw = make_uint2(opos, n_un ? upos0 : (wp.x != opos ? wp.x : wp.y));
+        else if (n_un > 1) nw = make_uint2(upos0, upos1);
+        else nw = make_uint2(upos0, wp.x != upos0 ? wp.x : wp.y);
+        if (nw.x != nw.y) *wslot = nw;
     }
     if (any_opp) return;
     int won = 0;
@@ -847,7 +1015,7 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
     won = __shfl_sync(FULL_MASK, won, 0);
     if (!won) return;
     const uint32_t x = ulit >> 1;
-    warp_mark_units(X, x);
+    if constexpr (MARK) warp_mark_units(X, x);
     if (X.cdl > 1u) {
         __threadfence_block();
         bool first = true;
@@ -865,6 +1033,12 @@ __device__ __forceinline__ void classify_long(const SweepCtx &X, uint32_t id, un
     if (lane == 0 && X.use_view) {
         __threadfence_block();
         view_set(X.V, x, (ulit & 1u) ? V_T : V_F);
+    }
+    if constexpr (MARK) {
+        if (X.chain) {
+            __syncwarp();
+            warp_push_units(X, x);
+        }
     }
 }
 
@@ -1014,21 +1188,26 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     // CTA); the literals and nogoods of the units checked are counted here
     bool queued = false, count_units = false, words = false;
     if constexpr (DQ == 1) {
-        if (!full && D.frontier == 2u) {
+        if (!full && D.frontier >= 2u) {
             const uint32_t nq = s_nq;
             queued = nq <= DQ_CAP;
             units = queued ? nq : ubase[BUCKET_MAX + 1];
             count_units = true;
+            X.chain = queued && D.frontier == 3u;
         }
     }
     if constexpr (DQ == 2) {
-        if (!full && D.frontier == 2u) {
+        if (!full && D.frontier >= 2u) {
             words = true;
             units = D.dirty_words;
             count_units = true;
         }
     }
     uint32_t pending = 0u, wbase = 0u;        // DQ = 2: units of the warp's word not yet run
+    // frontier = 3: waves of the queue; wave w pops positions [lo, units)
+    // with its own counter, and the units claims of wave w queued form wave
+    // w + 1 (up to DQ_WAVES waves)
+    uint32_t wave = 0u, lo = 0u;
     unsigned long long uvisits = 0;
     // Long and learned nogoods first (one warp each, round-robin over CTAs
     // first, then over the warps of a CTA); the warps that take one then
@@ -1038,7 +1217,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     const uint32_t wpc = blockDim.x >> 5, slot = (X.gw % wpc) * (X.nw / wpc) + X.gw / wpc;
     for (uint32_t i = slot; i < nl; i += X.nw) {
         uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
-        classify_long(X, id, checks);
+        classify_long<(DQ != 0)>(X, id, checks, D.nwatch ? D.nwatch + i : nullptr);
     }
     const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
     for (;;) {
@@ -1047,9 +1226,31 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
             u = wbase + (uint32_t)__ffs(pending) - 1u;
             pending &= pending - 1u;
         } else {
-            if (lane == 0) u = atomicAdd(uctr, 1u);
+            if (lane == 0) {
+                if constexpr (DQ == 1) u = X.chain ? lo + atomicAdd(&s_wave[wave], 1u) : atomicAdd(uctr, 1u);
+                else u = atomicAdd(uctr, 1u);
+            }
             u = __shfl_sync(FULL_MASK, u, 0);
-            if (u >= units) break;
+            if (u >= units) {
+                if constexpr (DQ == 1) {
+                    if (X.chain && wave + 1u < DQ_WAVES) {
+                        // every warp of the CTA arrives here once per wave;
+                        // the queue's length is read between two barriers, so
+                        // no warp pushes while it is read
+                        cta_sync();
+                        if (threadIdx.x == 0) s_ub[2] = min(s_nq, DQ_CAP);
+                        cta_sync();
+                        const uint32_t nq = s_ub[2];
+                        if (nq > units) {
+                            lo = units;
+                            units = nq;
+                            wave++;
+                            continue;
+                        }
+                    }
+                }
+                break;
+            }
             if constexpr (DQ == 1) {
                 if (queued) u = s_dq[u];
             }
@@ -1071,9 +1272,9 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         const uint32_t first = ubase[L];
         const uint32_t b0 = s_krange[L][0], b1 = s_krange[L][1];
         const uint32_t k0 = b0 + (u - first) * unit_groups(L) * 32u;
-        if (D.view_mode == VIEW_BYTES) run_unit_view<true>(X, L, k0, b1);
-        else if (D.view_mode == VIEW_PACKED) run_unit_view<false>(X, L, k0, b1);
-        else run_unit(X, L, k0, b1);
+        if (D.view_mode == VIEW_BYTES) run_unit_view<true, (DQ != 0)>(X, L, k0, b1);
+        else if (D.view_mode == VIEW_PACKED) run_unit_view<false, (DQ != 0)>(X, L, k0, b1);
+        else run_unit<(DQ != 0)>(X, L, k0, b1);
         if (count_units && lane == 0) {
             const uint32_t n = min(b1 - k0, unit_groups(L) * 32u);
             checks += (unsigned long long)L * n;
@@ -1098,6 +1299,12 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         cta_sync();
         const uint32_t n = min(s_ncl, CLAIM_BUF);
         if (threadIdx.x == 0) { s_unit = 0u; s_nq = 0u; }   // every warp has left the unit queue
+        if constexpr (DQ == 1) {
+            if (X.chain) {
+                for (uint32_t w = threadIdx.x; w < DQ_BITS / 32u; w += blockDim.x) s_dqbits[w] = 0u;
+                if (threadIdx.x < DQ_WAVES) s_wave[threadIdx.x] = 0u;
+            }
+        }
         if (threadIdx.x < 32u) {
             uint32_t base = 0;
             if (threadIdx.x == 0 && n) base = atomicAdd(&X.acc->nclaim, n);
@@ -1368,6 +1575,15 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
         }
     }
     cta_sync();
+}
+
+// Register learned nogood number i (its first literal at `id`, len
+// literals): the learned list, and its two watched positions (the first
+// two literals; a nogood of one literal is always scanned).
+__device__ __forceinline__ void add_learned(const Dev &D, uint32_t i, uint32_t id, uint32_t len)
+{
+    D.learned_ids[i] = id;
+    if (D.nwatch) D.nwatch[D.n_long + i] = len > 1u ? make_uint2(0u, 1u) : make_uint2(0u, 0u);
 }
 
 // Record of the last conflict analysis, for consistency checks (leader).
@@ -1691,8 +1907,10 @@ __device__ __forceinline__ void injected_stall(const Dev &D)
 // Algorithm 1 on the device.  rank/size: thread index and thread count of
 // the solving group; cta: this CTA's part of the program's static partition;
 // cta0/leader: the CTA and thread that run conflict analysis and write the
-// next control block.
-template <bool BATCH>
+// next control block.  UNITS: compiled with the frontier by units (used by
+// programs with frontier = 2; the kernels without it keep the sweeps free of
+// the unit marks).
+template <bool BATCH, bool UNITS>
 __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const View &V, uint32_t rank,
                                             uint32_t size, bool cta0, bool leader, uint32_t cta)
 {
@@ -1722,6 +1940,15 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     cta_sync();
     view_reload(D, V, 4u << (sC.round & 1u));
     unit_table(D, cta);
+    if constexpr (UNITS && !BATCH) {
+        // frontier by units: the CTA's unit range, no unit queued yet
+        if (threadIdx.x == 0 && D.frontier >= 2u) {
+            s_ub[0] = __ldg(D.cta_ubase + cta);
+            s_ub[1] = __ldg(D.cta_ubase + cta + 1u);
+            for (uint32_t w = 0; w < DQ_BITS / 32u; w++) s_dqbits[w] = 0u;
+            for (uint32_t w = 0; w < DQ_WAVES; w++) s_wave[w] = 0u;
+        }
+    }
     cta_sync();
 
     for (uint32_t k = 0;; k++) {
@@ -1830,7 +2057,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                                     N.op = OP_DONE; N.err = -6; N.status = 0;
                                     s_stop = 1u;
                                 } else {
-                                    D.learned_ids[N.n_learned] = lf;
+                                    add_learned(D, N.n_learned, lf, n);
                                     N.n_learned = N.n_learned + 1u;
                                     N.lfill = lf + n;
                                     N.op = OP_BACKJUMP;
@@ -1872,8 +2099,8 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 break;
             }
             // frontier by units: this round's dirty units of the CTA
-            if constexpr (!BATCH) {
-                if (D.frontier == 2u) build_unit_queue(D, cta, D.dirty + (C.round & 1u) * D.dirty_words, 0xFFFFFFFFu);
+            if constexpr (UNITS && !BATCH) {
+                if (D.frontier >= 2u) build_unit_queue(D, cta, D.dirty + (C.round & 1u) * D.dirty_words, 0xFFFFFFFFu);
             }
             // make last round's claims visible: clear their fresh bit
             // (grid-wide) and put them in this CTA's view
@@ -1892,7 +2119,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             cta_sync();
             sw = true; sw_cdl = C.cdl; sw_tbase = tend;
-            sw_full = C.full != 0u || D.frontier == 0u;
+            sw_full = C.full != 0u || D.frontier == 0u || (!UNITS && D.frontier >= 2u);
             sw_fr0 = C.tc; sw_fr1 = tend;
             if (leader) {
                 N.op = OP_ROUND; N.round = C.round + 1u; N.tc = tend; N.tb = tend; N.clean = 1; N.full = 0;
@@ -1923,7 +2150,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                     // (frontier by units: completion claims mark no units, so
                     // the next round sweeps everything)
                     N.op = OP_ROUND; N.round = C.round + 1u; N.tb = tend; N.tc = tend; N.clean = 0;
-                    N.full = D.frontier == 2u ? 1u : 0u;
+                    N.full = D.frontier >= 2u ? 1u : 0u;
                     atomicAdd(&D.stats->completions, 1ull);
                 }
                 break;
@@ -1945,9 +2172,9 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 atomicOr(D.asg + (bv >> 3), V_T << ((bv & 7u) * 4u));
             }
             if (threadIdx.x == 0) view_set(V, bv, V_T);
-            if (D.frontier == 2u) {
+            if (UNITS && D.frontier >= 2u) {
                 uint32_t *buf = D.dirty + (C.round & 1u) * D.dirty_words;
-                if constexpr (!BATCH) {
+                if constexpr (UNITS && !BATCH) {
                     build_unit_queue(D, cta, buf, bv);
                 } else if (threadIdx.x < 32u) {
                     // one program per CTA: the decision variable's units go
@@ -1961,7 +2188,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             }
             cta_sync();
             sw = true; sw_cdl = L; sw_tbase = tend + 1u; sw_dec = bv;
-            sw_full = D.frontier == 0u;
+            sw_full = D.frontier == 0u || (!UNITS && D.frontier >= 2u);
             if (leader) {
                 N.op = OP_ROUND; N.cdl = L; N.round = C.round + 1u; N.tc = tend + 1u; N.tb = tend + 1u;
                 N.clean = 0; N.full = 0;
@@ -2068,7 +2295,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                         for (uint32_t level = 2; level <= C.cdl; level++)
                             D.lits[C.lfill + n++] = mk_lit(__ldcg(D.dec_var + level), false);
                         D.lits[C.lfill + n - 1u] |= END_BIT;
-                        D.learned_ids[C.n_learned] = C.lfill;
+                        add_learned(D, C.n_learned, C.lfill, n);
                         N.n_learned = C.n_learned + 1u;
                         N.lfill = C.lfill + n;
                         N.op = OP_BACKJUMP;
@@ -2115,7 +2342,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             if (cta0) {
                 if (leader) {
                     D.lits[C.lfill + len - 1u] |= END_BIT;
-                    D.learned_ids[C.n_learned] = C.lfill;
+                    add_learned(D, C.n_learned, C.lfill, len);
                     __threadfence();
                 }
                 cta_sync();
@@ -2138,7 +2365,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                         N.lfill = lf;
                     } else {
                         uint32_t n = S.misc[2];
-                        D.learned_ids[C.n_learned + 1u] = lf;
+                        add_learned(D, C.n_learned + 1u, lf, n);
                         N.n_learned = C.n_learned + 2u;
                         N.lfill = lf + n;
                         N.op = OP_BACKJUMP;
@@ -2164,9 +2391,9 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         if (sw) {
             const unsigned long long ts = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
             SweepCtx X{&D, V, fresh_cur, sw_cdl, sw_tbase, acc, true, true, sw_dec, cta, rank >> 5, size >> 5};
-            if (D.frontier == 2u) X.dmark = D.dirty + ((C.round + 1u) & 1u) * D.dirty_words;
-            sweep<BATCH ? 2 : 1>(X, C.n_learned, sw_full, sw_fr0, sw_fr1, 0u,
-                                 D.frontier == 2u ? D.dirty + (C.round & 1u) * D.dirty_words : nullptr);
+            if (UNITS && D.frontier >= 2u) X.dmark = D.dirty + ((C.round + 1u) & 1u) * D.dirty_words;
+            sweep<UNITS ? (BATCH ? 2 : 1) : 0>(X, C.n_learned, sw_full, sw_fr0, sw_fr1, 0u,
+                                               D.frontier >= 2u ? D.dirty + (C.round & 1u) * D.dirty_words : nullptr);
             if (threadIdx.x == 0) atomicMax(&acc->tsweep, globaltimer_ns() - ts);
         }
 

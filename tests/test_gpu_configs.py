@@ -56,7 +56,7 @@ def _golden():
 
 # ------------------------------------------------------------ tiny programs
 
-@pytest.mark.parametrize("fr", [0, 2])
+@pytest.mark.parametrize("fr", [0, 2, 3])
 def test_tiny_programs_all_1000_seeds(gpu, fr):
     golden = _golden()
     assert sorted(golden) == list(range(1000))
@@ -73,10 +73,11 @@ def test_tiny_programs_all_1000_seeds(gpu, fr):
     print(f"tiny programs: 1000 seeds, {models_total} answer sets, all equal to brute force")
 
 
-def test_tiny_programs_all_1000_seeds_batched(gpu):
+@pytest.mark.parametrize("fr", [0, 2])
+def test_tiny_programs_all_1000_seeds_batched(gpu, fr):
     golden = _golden()
     progs = [tiny_program(i) for i in range(1000)]
-    P = [gpu.Program(p) for p in progs]
+    P = [gpu.Program(p, frontier=fr) for p in progs]
     st, nm, models = gpu.solve_batch(P, max_models_each=0, cap_each=64)
     for i, p in enumerate(progs):
         want = golden[i]

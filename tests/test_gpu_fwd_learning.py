@@ -241,7 +241,7 @@ def test_fwd_learned_nogood_recomputed(gpu, atoms, rules, seed, k, mode):
 
 @pytest.mark.parametrize("grid", [1, 5, 0])
 @pytest.mark.parametrize("k", [3, 11])
-@pytest.mark.parametrize("fr", [0, 1, 2])
+@pytest.mark.parametrize("fr", [0, 1, 2, 3])
 def test_fwd_learned_nogood_recomputed_grids_and_frontiers(gpu, grid, k, fr):
     prog = random_program(2000, 5000, program_seed(705, 2))
     P = gpu.Program(prog, conflict_budget=k, grid_ctas=grid, frontier=fr, time_budget_ms=60_000)

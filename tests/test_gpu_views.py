@@ -133,7 +133,7 @@ def test_batch_in_every_view(gpu, mode):
             assert oracle.is_answer_set(p, m)
 
 
-@pytest.mark.parametrize("fr", [1, 2])
+@pytest.mark.parametrize("fr", [1, 2, 3])
 @pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("grid", [1, 5, 0])
 @pytest.mark.parametrize("seed", range(5))
@@ -159,7 +159,7 @@ def test_frontier_propagation_reaches_the_same_fixpoint(gpu, fr, mode, grid, see
             assert (clo == oclo[perm]).all()
 
 
-@pytest.mark.parametrize("fr", [1, 2])
+@pytest.mark.parametrize("fr", [1, 2, 3])
 @pytest.mark.parametrize("index", [3, 77, 151, 402, 555, 918])
 def test_frontier_tiny_full_enumeration(gpu, fr, index):
     prog = tiny_program(index)
@@ -168,7 +168,7 @@ def test_frontier_tiny_full_enumeration(gpu, fr, index):
     assert _sets(models) == want and n == len(want)
 
 
-@pytest.mark.parametrize("fr", [1, 2])
+@pytest.mark.parametrize("fr", [1, 2, 3])
 @pytest.mark.parametrize("seed", range(4))
 def test_frontier_search_answers_and_bitmaps(gpu, fr, seed):
     prog = random_program(700, 1400, program_seed(609, seed))
@@ -196,7 +196,7 @@ def test_frontier_search_answers_and_bitmaps(gpu, fr, seed):
         assert (deps[v, :nw] == want).all(), v
 
 
-@pytest.mark.parametrize("fr", [1, 2])
+@pytest.mark.parametrize("fr", [1, 2, 3])
 def test_frontier_batch(gpu, fr):
     progs = batch_programs(10, rules_per_atom=2, lo=50, hi=1500, config_id=610)
     P = [gpu.Program(p, frontier=fr, time_budget_ms=20_000) for p in progs]
