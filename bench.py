@@ -61,6 +61,7 @@ def _args():
     ap.add_argument("--learned", type=int, default=256,
                     help="held-out programs for the learned-heuristic comparison; 0 = skip")
     ap.add_argument("--learned-train", type=int, default=1024, help="training programs (traces)")
+    ap.add_argument("--learned-seeds", type=int, default=1, help="disjoint held-out sets evaluated")
     ap.add_argument("--no-learning-compare", action="store_true",
                     help="skip the fwd-learning vs first-UIP resolution comparison")
     ap.add_argument("--big-atoms", type=int, default=400_000,
@@ -168,7 +169,7 @@ def _traffic(kernel_src_sha, checks_per_launch, atoms, rules):
 
 def _src_sha():
     h = hashlib.sha256()
-    for f in ("solver.cuh", "solve.cu", "sweep.cu", "device.cuh", "store.cpp", "store.h", "api.cpp"):
+    for f in ("solver.cuh", "kernels.cuh", "solve.cu", "sweep.cu", "device.cuh", "store.cpp", "store.h", "api.cpp"):
         h.update(open(os.path.join(ROOT, "paper_1909_01786_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -717,48 +718,56 @@ def _learned(a, aspgpu, torch):
     t_train = time.perf_counter() - t0
     if a.save_weights:
         H.save(w, a.save_weights, **tstats)
-    evalp = _a11_programs(a.learned, 2 * 10**6)
-    out = {}
-    for name, kw in (("plain", dict(heuristic=0)), ("learned", dict(heuristic=2, mlp_weights=w)),
-                     ("learned_static", dict(heuristic=3, mlp_weights=ws))):
-        P = [aspgpu.Program(p, conflict_budget=budget, time_budget_ms=20_000, deps_levels=1024,
-                            learned_capacity=1 << 20, **kw) for p in evalp]
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        st, nm, models = aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t
-        dec = sum(q.stats()["decisions"] for q in P)
-        con = sum(q.stats()["conflicts"] for q in P)
-        solved = int(((st == 10) | (st == 20)).sum())
-        out[name] = {"seconds": dt, "solved": solved, "solved_per_s": solved / dt,
-                     "decisions": int(dec), "conflicts": int(con), "statuses": st.copy(), "models": models}
-        for q in P:
-            q.close()
-    # zero mismatches: where both decided they agree; models are answer sets
+    import numpy as np
     import oracle
-    sp = out["plain"]["statuses"]
-    mism = 0
-    for name in ("learned", "learned_static"):
-        sl = out[name]["statuses"]
-        both = ((sp == 10) | (sp == 20)) & ((sl == 10) | (sl == 20))
-        mism += int((sp[both] != sl[both]).sum())
-    checked = bad = 0
-    for name in ("plain", "learned", "learned_static"):
-        for i, m in enumerate(out[name]["models"]):
-            if len(m):
-                checked += 1
-                bad += not oracle.is_answer_set(evalp[i], m[0])
-    for name in ("plain", "learned", "learned_static"):
-        del out[name]["statuses"], out[name]["models"]
-    return {"workload": f"{a.learned} held-out programs (half random, 4 rules per atom, 200-2000 atoms; "
-                        f"half 3-colourings, 40-400 vertices), conflict budget {budget}, batched",
+    names = ("plain", "learned", "learned_static")
+    per_seed = []
+    mism = checked = bad = 0
+    for seed in range(a.learned_seeds):
+        evalp = _a11_programs(a.learned, 2 * 10**6 + seed * 10**5)
+        out = {}
+        for name, kw in zip(names, (dict(heuristic=0), dict(heuristic=2, mlp_weights=w),
+                                    dict(heuristic=3, mlp_weights=ws))):
+            P = [aspgpu.Program(p, conflict_budget=budget, time_budget_ms=20_000, deps_levels=1024,
+                                learned_capacity=1 << 20, **kw) for p in evalp]
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st, nm, models = aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            dec = sum(q.stats()["decisions"] for q in P)
+            con = sum(q.stats()["conflicts"] for q in P)
+            solved = int(((st == 10) | (st == 20)).sum())
+            out[name] = {"seconds": dt, "solved": solved, "solved_per_s": solved / dt,
+                         "decisions": int(dec), "conflicts": int(con), "statuses": st.copy(), "models": models}
+            for q in P:
+                q.close()
+        # zero mismatches: where both decided they agree; models are answer sets
+        sp = out["plain"]["statuses"]
+        for name in ("learned", "learned_static"):
+            sl = out[name]["statuses"]
+            both = ((sp == 10) | (sp == 20)) & ((sl == 10) | (sl == 20))
+            mism += int((sp[both] != sl[both]).sum())
+        for name in names:
+            for i, m in enumerate(out[name]["models"]):
+                if len(m):
+                    checked += 1
+                    bad += not oracle.is_answer_set(evalp[i], m[0])
+            del out[name]["statuses"], out[name]["models"]
+        per_seed.append(out)
+    ratio = lambda name: [o[name]["solved_per_s"] / o["plain"]["solved_per_s"] if o["plain"]["solved"] else None
+                          for o in per_seed]
+    first = per_seed[0]
+    r_l, r_s = ratio("learned"), ratio("learned_static")
+    spread = lambda r: [min(x for x in r if x is not None), max(x for x in r if x is not None)] \
+        if any(x is not None for x in r) else None
+    return {"workload": f"{a.learned_seeds} x {a.learned} held-out programs (half random, 4 rules per atom, "
+                        f"200-2000 atoms; half 3-colourings, 40-400 vertices), conflict budget {budget}, batched",
             "training": {"programs": a.learned_train, "seconds": t_train, **tstats},
-            **out, "status_mismatches": mism, "models_checked": checked, "invalid_models": bad,
-            "speedup_solved_per_s": (out["learned"]["solved_per_s"] / out["plain"]["solved_per_s"])
-            if out["plain"]["solved"] else None,
-            "speedup_static_solved_per_s": (out["learned_static"]["solved_per_s"] / out["plain"]["solved_per_s"])
-            if out["plain"]["solved"] else None,
+            **first, "per_seed": per_seed if a.learned_seeds > 1 else None,
+            "status_mismatches": mism, "models_checked": checked, "invalid_models": bad,
+            "speedup_solved_per_s": r_l[0], "speedup_static_solved_per_s": r_s[0],
+            "speedup_spread": {"learned": spread(r_l), "learned_static": spread(r_s)},
             "static_training": sstats}
 
 

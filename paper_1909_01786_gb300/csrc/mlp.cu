@@ -1,9 +1,10 @@
 // Training of the learned decision heuristic (not in the paper): a 16-64-1
 // MLP, ReLU hidden layer, logistic output, trained by minibatch SGD with
-// momentum on binary cross-entropy, in one CTA.  One lane holds one sample;
-// gradients are reduced across the warp with shuffles and summed into shared
-// memory.  The solver evaluates the trained network with bf16 weights and
-// fp32 accumulation (solver.cuh, mlp_score).
+// momentum on binary cross-entropy.  Each minibatch is spread over many
+// CTAs, one sample per thread: gradients are reduced across the warp with
+// shuffles, summed into shared memory, then added to a global gradient; a
+// second kernel applies the momentum step.  The solver evaluates the trained
+// network with bf16 weights and fp32 accumulation (solver.cuh, mlp_score).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -30,67 +31,68 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(1024, 1) mlp_train_kernel(const float *X, const float *Y, int n, int epochs,
-                                                            int batch, float lr, float momentum, float *W)
+// Gradient of the mean binary cross-entropy over samples [i0, i1), added to
+// g.  One sample per thread (grid-stride); every warp runs the same number
+// of iterations so the shuffles see all 32 lanes.
+__global__ void __launch_bounds__(256) mlp_grad_kernel(const float *X, const float *Y, int i0, int i1, const float *W,
+                                                       float *g)
 {
-    __shared__ float w[MLP_PARAMS], g[MLP_PARAMS], v[MLP_PARAMS];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    float *W1 = w, *b1 = w + N_FEATURES * N_HIDDEN, *w2 = b1 + N_HIDDEN, *b2 = w2 + N_HIDDEN;
-    for (int p = tid; p < MLP_PARAMS; p += blockDim.x) { w[p] = W[p]; v[p] = 0.0f; }
+    __shared__ float w[MLP_PARAMS], gs[MLP_PARAMS];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int p = tid; p < MLP_PARAMS; p += blockDim.x) { w[p] = W[p]; gs[p] = 0.0f; }
     __syncthreads();
-    for (int ep = 0; ep < epochs; ep++) {
-        for (int b0 = 0; b0 < n; b0 += batch) {
-            const int b1i = b0 + batch < n ? b0 + batch : n;
-            const float inv = 1.0f / (float)(b1i - b0);
-            for (int p = tid; p < MLP_PARAMS; p += blockDim.x) g[p] = 0.0f;
-            __syncthreads();
-            for (int s0 = b0 + wid * 32; s0 < b1i; s0 += nw * 32) {
-                const int i = s0 + lane;
-                const bool ok = i < b1i;
-                float x[N_FEATURES];
+    const float *W1 = w, *b1 = w + N_FEATURES * N_HIDDEN, *w2 = b1 + N_HIDDEN, *b2 = w2 + N_HIDDEN;
+    const float inv = 1.0f / (float)(i1 - i0);
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = i0 + blockIdx.x * blockDim.x + (tid & ~31); base < i1; base += stride) {
+        const int i = base + lane;
+        const bool ok = i < i1;
+        float x[N_FEATURES];
 #pragma unroll
-                for (int q = 0; q < N_FEATURES; q++) x[q] = ok ? X[(size_t)i * N_FEATURES + q] : 0.0f;
-                // forward
-                float logit = b2[0];
-                for (int k = 0; k < N_HIDDEN; k++) {
-                    float a = b1[k];
+        for (int q = 0; q < N_FEATURES; q++) x[q] = ok ? X[(size_t)i * N_FEATURES + q] : 0.0f;
+        float logit = b2[0];
+        for (int k = 0; k < N_HIDDEN; k++) {
+            float a = b1[k];
 #pragma unroll
-                    for (int q = 0; q < N_FEATURES; q++) a = fmaf(W1[k * N_FEATURES + q], x[q], a);
-                    logit = fmaf(w2[k], fmaxf(a, 0.0f), logit);
-                }
-                const float p = 1.0f / (1.0f + expf(-logit));
-                const float d = ok ? (p - Y[i]) * inv : 0.0f;        // dLoss/dlogit
-                // backward, reduced over the warp's 32 samples
-                const float gb2 = warp_sum(d);
-                if (lane == 0) atomicAdd(&g[MLP_PARAMS - 1], gb2);
-                for (int k = 0; k < N_HIDDEN; k++) {
-                    float a = b1[k];
+            for (int q = 0; q < N_FEATURES; q++) a = fmaf(W1[k * N_FEATURES + q], x[q], a);
+            logit = fmaf(w2[k], fmaxf(a, 0.0f), logit);
+        }
+        const float p = 1.0f / (1.0f + expf(-logit));
+        const float d = ok ? (p - Y[i]) * inv : 0.0f;        // dLoss/dlogit
+        const float gb2 = warp_sum(d);
+        if (lane == 0) atomicAdd(&gs[MLP_PARAMS - 1], gb2);
+        for (int k = 0; k < N_HIDDEN; k++) {
+            float a = b1[k];
 #pragma unroll
-                    for (int q = 0; q < N_FEATURES; q++) a = fmaf(W1[k * N_FEATURES + q], x[q], a);
-                    const float h = fmaxf(a, 0.0f);
-                    const float dh = a > 0.0f ? d * w2[k] : 0.0f;
-                    const float gw2 = warp_sum(d * h);
-                    const float gb1 = warp_sum(dh);
-                    if (lane == 0) {
-                        atomicAdd(&g[N_FEATURES * N_HIDDEN + N_HIDDEN + k], gw2);
-                        atomicAdd(&g[N_FEATURES * N_HIDDEN + k], gb1);
-                    }
-#pragma unroll
-                    for (int q = 0; q < N_FEATURES; q++) {
-                        const float gw = warp_sum(dh * x[q]);
-                        if (lane == 0) atomicAdd(&g[k * N_FEATURES + q], gw);
-                    }
-                }
+            for (int q = 0; q < N_FEATURES; q++) a = fmaf(W1[k * N_FEATURES + q], x[q], a);
+            const float h = fmaxf(a, 0.0f);
+            const float dh = a > 0.0f ? d * w2[k] : 0.0f;
+            const float gw2 = warp_sum(d * h);
+            const float gb1 = warp_sum(dh);
+            if (lane == 0) {
+                atomicAdd(&gs[N_FEATURES * N_HIDDEN + N_HIDDEN + k], gw2);
+                atomicAdd(&gs[N_FEATURES * N_HIDDEN + k], gb1);
             }
-            __syncthreads();
-            for (int p = tid; p < MLP_PARAMS; p += blockDim.x) {
-                v[p] = momentum * v[p] + g[p];
-                w[p] -= lr * v[p];
+#pragma unroll
+            for (int q = 0; q < N_FEATURES; q++) {
+                const float gw = warp_sum(dh * x[q]);
+                if (lane == 0) atomicAdd(&gs[k * N_FEATURES + q], gw);
             }
-            __syncthreads();
         }
     }
-    for (int p = tid; p < MLP_PARAMS; p += blockDim.x) W[p] = w[p];
+    __syncthreads();
+    for (int p = tid; p < MLP_PARAMS; p += blockDim.x)
+        if (gs[p] != 0.0f) atomicAdd(&g[p], gs[p]);
+}
+
+// SGD with momentum: v = momentum v + g, W -= lr v; the gradient is cleared.
+__global__ void mlp_update_kernel(float *W, float *g, float *v, float lr, float momentum)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= MLP_PARAMS) return;
+    v[p] = momentum * v[p] + g[p];
+    W[p] -= lr * v[p];
+    g[p] = 0.0f;
 }
 
 // Inference with the solver's arithmetic: bf16 weights, fp32 accumulation.
@@ -187,17 +189,29 @@ extern "C" int asp_train_mlp(const float *features, const float *labels, int64_t
     float *dX = nullptr, *dY = nullptr, *dW = nullptr;
     const size_t bx = (size_t)n * N_FEATURES * sizeof(float), by = (size_t)n * sizeof(float);
     const size_t bw = (size_t)MLP_PARAMS * sizeof(float);
-    if (cudaMalloc(&dX, bx) != cudaSuccess || cudaMalloc(&dY, by) != cudaSuccess || cudaMalloc(&dW, bw) != cudaSuccess) {
+    // dW holds the weights, then the gradient and the momentum
+    if (cudaMalloc(&dX, bx) != cudaSuccess || cudaMalloc(&dY, by) != cudaSuccess ||
+        cudaMalloc(&dW, 3 * bw) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(dX); cudaFree(dY); cudaFree(dW);
         return internal_fail(ASP_E_OOM, "device allocation failed (training data)");
     }
+    float *dG = dW + MLP_PARAMS, *dV = dW + 2 * MLP_PARAMS;
     cudaError_t e = cudaMemcpy(dX, features, bx, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dY, labels, by, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dW, weights, bw, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        mlp_train_kernel<<<1, 1024>>>(dX, dY, (int)n, epochs, 4096, learning_rate, 0.9f, dW);
-        e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemset(dG, 0, 2 * bw);
+    // minibatches of 4096 samples, one sample per thread: 16 CTAs of 256
+    const int batch = 4096, threads = 256;
+    const int updates = (MLP_PARAMS + 255) / 256;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ep++) {
+        for (int64_t b0 = 0; b0 < n && e == cudaSuccess; b0 += batch) {
+            const int b1 = (int)std::min<int64_t>(b0 + batch, n);
+            const int ctas = (b1 - (int)b0 + threads - 1) / threads;
+            mlp_grad_kernel<<<ctas, threads>>>(dX, dY, (int)b0, b1, dW, dG);
+            mlp_update_kernel<<<updates, 256>>>(dW, dG, dV, learning_rate, 0.9f);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(weights, dW, bw, cudaMemcpyDeviceToHost);

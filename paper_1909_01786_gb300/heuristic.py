@@ -53,18 +53,21 @@ def split(w):
     return W1, b1, w2, b2
 
 
-def collect_traces(programs, conflict_budget: int = 200, trace_capacity: int = 4096, **kw):
-    """Solve programs (batched, plain heuristic) and gather (features, labels)."""
-    P = [aspgpu.Program(p, conflict_budget=conflict_budget, trace_capacity=trace_capacity,
-                        deps_levels=1024, learned_capacity=1 << 20, **kw) for p in programs]
-    aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
+def collect_traces(programs, conflict_budget: int = 200, trace_capacity: int = 4096, chunk: int = 2048, **kw):
+    """Solve programs (batched, plain heuristic, `chunk` programs loaded at a
+    time) and gather (features, labels)."""
     X, y = [], []
-    for q in P:
-        f, lab = q.trace(trace_capacity)
-        keep = lab >= 0
-        X.append(f[keep])
-        y.append(lab[keep])
-        q.close()
+    programs = list(programs)
+    for c0 in range(0, len(programs), chunk):
+        P = [aspgpu.Program(p, conflict_budget=conflict_budget, trace_capacity=trace_capacity,
+                            deps_levels=1024, learned_capacity=1 << 20, **kw) for p in programs[c0:c0 + chunk]]
+        aspgpu.solve_batch(P, max_models_each=1, cap_each=1)
+        for q in P:
+            f, lab = q.trace(trace_capacity)
+            keep = lab >= 0
+            X.append(f[keep])
+            y.append(lab[keep])
+            q.close()
     return np.concatenate(X) if X else np.zeros((0, N_FEATURES), np.float32), \
         np.concatenate(y).astype(np.float32) if y else np.zeros(0, np.float32)
 
