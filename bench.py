@@ -71,7 +71,8 @@ def _args():
     ap.add_argument("--batch-ms", type=int, default=2000,
                     help="device time budget per program of the batched leg (the oracle gets the same in CPU time)")
     ap.add_argument("--batch-frontier", type=int, default=2,
-                    help="propagation rounds of the batched leg (0 full sweeps, 2 the unit frontier)")
+                    help="propagation rounds of the one-at-a-time comparison and of an explicitly configured "
+                         "batch (0 full sweeps, 2 the unit frontier); the autotuned batch chooses its own")
     ap.add_argument("--batch-rules-per-atom", type=int, default=2,
                     help="rules per atom of the batched workload (2: the family decides within the budget)")
     ap.add_argument("--sweep-only", type=int, default=0,
@@ -468,21 +469,36 @@ def shard_bounds(count, rank, world):
 
 
 def _oracle_first(args):
-    prog, budget_s = args
+    prog, budget_s, conflicts = args
     import oracle
     t = time.perf_counter()
-    st, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=budget_s)
+    st, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=budget_s, conflict_budget=conflicts)
     return st, time.perf_counter() - t
 
 
-def _oracle_pool(progs, budget_s):
+def _oracle_pool(progs, budget_s, conflicts=0):
     """The oracle's CDNL, one program per host core (spawned workers)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_first, [(p, budget_s) for p in progs], chunksize=4)
+        res = pool.map(_oracle_first, [(p, budget_s, conflicts) for p in progs], chunksize=4)
     return [r[0] for r in res], [r[1] for r in res], time.perf_counter() - t0, cores
+
+
+def _oracle_enumerate(prog):
+    import oracle
+    return len(oracle.brute_force(prog))
+
+
+def _oracle_pool_enumerate(progs):
+    """The oracle's brute force (every answer set), one program per host core."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        n = pool.map(_oracle_enumerate, progs, chunksize=1)
+    return sum(n), time.perf_counter() - t0, cores
 
 
 def _batched(a, aspgpu, torch, rank=0, world=1, device=None):
@@ -644,13 +660,18 @@ def _tiny(a, aspgpu, torch):
     t0 = time.perf_counter()
     n_bf = sum(len(oracle.brute_force(p)) for p in sample)
     tbf = time.perf_counter() - t0
+    pool_sample = progs[:64]
+    n_pool, t_pool, cores = _oracle_pool_enumerate(pool_sample)
     return {"workload": f"{a.tiny} tiny programs (20 atoms, 40 rules, 3 constraints), every answer set",
             "answer_sets": int(nm.sum()), "answer_sets_plain": int(n_plain),
             "batched": {"seconds": tb, "instances_per_s": a.tiny / tb},
             "plain": {"seconds": tp, "instances_per_s": a.tiny / tp},
             "cpu_baseline": {"kind": "oracle brute force over 2^20 interpretations", "cores": 1,
                              "sample": f"first {len(sample)} programs ({n_bf} answer sets)",
-                             "instances_per_s": len(sample) / tbf}}
+                             "instances_per_s": len(sample) / tbf},
+            "oracle_all_cores": {"kind": "oracle brute force, one program per host core", "cores": cores,
+                                 "sample": f"first {len(pool_sample)} programs ({n_pool} answer sets)",
+                                 "instances_per_s": len(pool_sample) / t_pool}}
 
 
 def _work_ratios(out):
@@ -679,14 +700,16 @@ def _summary(out):
         "big_store_sweep_frac": g(out, "big_store", "sweep", "frac_of_hbm"),
         "big_store_solver_frac": g(out, "big_store", "solver", "frac_of_hbm"),
         "tiny_instances_per_s": [g(out, "tiny_programs", "batched", "instances_per_s"),
-                                 g(out, "tiny_programs", "plain", "instances_per_s")],
+                                 g(out, "tiny_programs", "plain", "instances_per_s"),
+                                 g(out, "tiny_programs", "oracle_all_cores", "instances_per_s")],
         "batched_solved": [g(out, "batched", "batched", "solved"), g(out, "batched", "plain", "solved"),
                            g(out, "batched", "oracle_all_cores", "solved")],
         "batched_speedup": g(out, "batched", "speedup_solved_per_s"),
         "batched_oracle_mismatches": g(out, "batched", "oracle_all_cores", "status_mismatches"),
         "learned_solved": [g(out, "learned_heuristic", "plain", "solved"),
                            g(out, "learned_heuristic", "learned", "solved"),
-                           g(out, "learned_heuristic", "learned_static", "solved")],
+                           g(out, "learned_heuristic", "learned_static", "solved"),
+                           g(out, "learned_heuristic", "oracle_all_cores", "solved")],
         "learned_speedup": [g(out, "learned_heuristic", "speedup_solved_per_s"),
                             g(out, "learned_heuristic", "speedup_static_solved_per_s")],
         "frontier_decisions_per_s": {k: g(out, "frontier_compare", k, "decisions_per_s")
@@ -758,13 +781,20 @@ def _learned(a, aspgpu, torch):
     ratio = lambda name: [o[name]["solved_per_s"] / o["plain"]["solved_per_s"] if o["plain"]["solved"] else None
                           for o in per_seed]
     first = per_seed[0]
+    # the oracle's CDNL on every host core, same held-out programs and
+    # conflict budget (first seed set)
+    ost, _, owall, cores = _oracle_pool(_a11_programs(a.learned, 2 * 10**6), 20.0, conflicts=budget)
+    ost = np.array(ost)
+    osolved = int(((ost == 10) | (ost == 20)).sum())
+    oracle_part = {"solved": osolved, "seconds": owall, "cores": cores, "solved_per_s": osolved / owall,
+                   "budget": f"{budget} conflicts (and 20 s) per program"}
     r_l, r_s = ratio("learned"), ratio("learned_static")
     spread = lambda r: [min(x for x in r if x is not None), max(x for x in r if x is not None)] \
         if any(x is not None for x in r) else None
     return {"workload": f"{a.learned_seeds} x {a.learned} held-out programs (half random, 4 rules per atom, "
                         f"200-2000 atoms; half 3-colourings, 40-400 vertices), conflict budget {budget}, batched",
             "training": {"programs": a.learned_train, "seconds": t_train, **tstats},
-            **first, "per_seed": per_seed if a.learned_seeds > 1 else None,
+            **first, "per_seed": per_seed if a.learned_seeds > 1 else None, "oracle_all_cores": oracle_part,
             "status_mismatches": mism, "models_checked": checked, "invalid_models": bad,
             "speedup_solved_per_s": r_l[0], "speedup_static_solved_per_s": r_s[0],
             "speedup_spread": {"learned": spread(r_l), "learned_static": spread(r_s)},

@@ -240,16 +240,20 @@ typedef struct asp_batch asp_batch;
 #define ASP_BATCH_AUTOTUNE (-1)   /* let the autotuner choose the configuration */
 
 /* Prepare repeated batched solving of n loaded programs: uploads one
- * descriptor per program, chooses the kernel configuration and captures the
- * launch (queue reset + batch kernel) in a CUDA graph.  Configurations:
- * 0 = 256 threads per CTA, 3 CTAs per SM; 1 = 128 threads, 6 per SM (twice
- * the programs in flight, smaller shared-memory views).  config =
- * ASP_BATCH_AUTOTUNE runs each configuration once on a sample of up to 256
- * programs spread over the queue (each with at most 8 conflicts and 0.5 s of
- * device time) and keeps the one with the lower device time per program (the trial solves change nothing but the programs' last
- * results).  models_cap may be NULL (no models kept).  The programs must
- * stay loaded until asp_batch_free.  Errors: ASP_E_ARG, ASP_E_OOM,
- * ASP_E_CUDA. */
+ * descriptor per program, chooses the kernel configuration and the
+ * propagation schedule, and captures the launch (queue reset + batch
+ * kernel) in a CUDA graph.  Configurations: 0 = 256 threads per CTA, 3 CTAs
+ * per SM; 1 = 128 threads, 6 per SM (twice the programs in flight, smaller
+ * shared-memory views).  With an explicit configuration each program keeps
+ * its own frontier option.  config = ASP_BATCH_AUTOTUNE tries every schedule
+ * -- each configuration with full sweeps and, where the programs are small
+ * enough to have the lists (about 20k atoms at 4 rules per atom), with the
+ * frontier by units -- once on a sample of up to 256 programs spread over
+ * the queue (each with at most 8 conflicts and 0.5 s of device time), and
+ * keeps the one with the lowest device time per program (the trial solves
+ * change nothing but the programs' last results).  models_cap may be NULL
+ * (no models kept).  The programs must stay loaded until asp_batch_free.
+ * Errors: ASP_E_ARG, ASP_E_OOM, ASP_E_CUDA. */
 int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each, const int64_t *models_cap,
                      int32_t config, asp_batch **out);
 
@@ -258,11 +262,14 @@ int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each,
  * when the capacity given at creation is 0). */
 int asp_batch_run(asp_batch *b, int32_t *statuses, int64_t *n_models, uint64_t *const *models);
 
-/* The configuration in use (0 or 1), its threads per CTA, the grid, and the
- * autotuner's device time per program of configurations 0 and 1 (ns; 0 if
- * not measured, < 0 if it could not run); any output may be NULL. */
+/* The configuration in use (0 or 1), its threads per CTA, the grid, the
+ * propagation schedule (ASP_FRONTIER_UNITS for programs with unit lists, or
+ * ASP_FRONTIER_FULL), and trial_ns (host double[4]): the autotuner's device
+ * time per program of configurations 0 and 1 with full sweeps, then 0 and 1
+ * with the unit frontier (ns; 0 if not tried, < 0 if it could not run); any
+ * output may be NULL. */
 int asp_batch_info(const asp_batch *b, int32_t *config, int32_t *block_threads, int32_t *grid,
-                   double *trial_ns);
+                   int32_t *frontier, double *trial_ns);
 
 /* Release the batch's descriptors, graph and stream (not the programs). */
 void asp_batch_free(asp_batch *b);

@@ -96,7 +96,7 @@ def lib(build_if_missing: bool = True):
         L.asp_batch_create.restype = C.c_int
         L.asp_batch_run.argtypes = [vp, vp, vp, vp]
         L.asp_batch_run.restype = C.c_int
-        L.asp_batch_info.argtypes = [vp, vp, vp, vp, vp]
+        L.asp_batch_info.argtypes = [vp, vp, vp, vp, vp, vp]
         L.asp_batch_info.restype = C.c_int
         L.asp_batch_free.argtypes = [vp]
         L.asp_batch_free.restype = None
@@ -389,11 +389,12 @@ class BatchPlan:
         return st, nm, models
 
     def info(self):
-        cfg, bt, grid = C.c_int32(), C.c_int32(), C.c_int32()
-        trial = (C.c_double * 2)()
-        _check(lib().asp_batch_info(self.handle, C.byref(cfg), C.byref(bt), C.byref(grid), trial))
+        cfg, bt, grid, fr = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        trial = (C.c_double * 4)()
+        _check(lib().asp_batch_info(self.handle, C.byref(cfg), C.byref(bt), C.byref(grid), C.byref(fr), trial))
         return {"config": cfg.value, "block_threads": bt.value, "grid": grid.value,
-                "trial_ns_per_program": [trial[0], trial[1]]}
+                "frontier": {FRONTIER_FULL: "full", FRONTIER_UNITS: "units"}.get(fr.value, fr.value),
+                "trial_ns_per_program": {"full": [trial[0], trial[1]], "units": [trial[2], trial[3]]}}
 
     def close(self):
         if self.handle:

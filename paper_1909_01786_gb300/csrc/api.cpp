@@ -362,8 +362,12 @@ static int plan_grid(asp_prog *p, const HostStore &H)
 // configuration (3 or 6 CTAs in an SM's 228 KB, less reserved and static
 // shared memory).
 constexpr size_t BATCH_SMEM_BUDGET[2] = {72 * 1024 - 1024, 34 * 1024};
-// frontier by units in batches: programs of at most this many sweep units
-constexpr uint64_t BATCH_MAX_UNITS = 1u << 16;
+// frontier by units in batches: the unit lists of a program's single-CTA
+// partition are built for programs of at most this many sweep units (about
+// 20k atoms at 4 rules per atom), whatever the program's own frontier option,
+// so that the batch autotuner can choose between full sweeps and the unit
+// frontier
+constexpr uint64_t BATCH_MAX_UNITS = 1u << 14;
 
 static int plan_batch(asp_prog *p, const HostStore &H, int config)
 {
@@ -379,14 +383,17 @@ static int plan_batch(asp_prog *p, const HostStore &H, int config)
     D1.cta_boff = upload(p, boff, rc);
     if (rc == ASP_OK) D1.cta_auxlo = upload(p, alo, rc);
     if (rc == ASP_OK) D1.cta_auxn = upload(p, an, rc);
-    if (rc == ASP_OK && p->D.frontier >= 2) {
+    if (rc == ASP_OK) {
         // one program per CTA: the units of the whole store (the same for
-        // both configurations); programs too large for batches keep full
-        // sweeps there
+        // both configurations), for programs small enough for batches.  The
+        // descriptor keeps the program's own choice (the unit frontier if
+        // it asked for it and the lists exist, no chaining in batches); a
+        // batch's autotuner may switch every program with lists to it
         if (config == 0) rc = unit_lists(p, H, boff, 1u, BATCH_MAX_UNITS, p->batch_units);
         if (rc == ASP_OK) {
+            const uint32_t own = D1.frontier;
             use_unit_lists(D1, p->batch_units);
-            D1.frontier = p->batch_units.built ? 2u : 0u;    // no chaining in batches
+            D1.frontier = own >= 2u ? (p->batch_units.built ? 2u : 0u) : own;
         }
     }
     p->D1[config] = D1;
@@ -402,9 +409,11 @@ struct asp_batch {
     std::vector<int64_t> caps;
     int64_t max_models_each = 0;
     int config = 0, grid = 0;
-    bool units = false;                 // some program sweeps by the frontier by units
+    bool units = false;                 // the unit-frontier kernels (programs with unit lists use them)
     size_t smem = 0;
-    double trial_ns[2] = {0.0, 0.0};
+    // autotuner trial times per program: configurations 0 and 1 with full
+    // sweeps, then with the unit frontier (0 = not tried, < 0 = cannot run)
+    double trial_ns[4] = {0.0, 0.0, 0.0, 0.0};
     uint32_t queued = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -429,6 +438,10 @@ std::vector<Dev> batch_descriptors(const asp_batch *b, int config, bool trial = 
     for (size_t i = 0; i < b->progs.size(); i++) {
         asp_prog *p = b->progs[i];
         Dev d = p->D1[config];
+        // the batch's propagation schedule: the unit frontier for programs
+        // with lists, or no unit frontier at all
+        if (b->units && p->batch_units.built) d.frontier = 2u;
+        else if (!b->units && d.frontier >= 2u) d.frontier = 0u;
         d.mode = MODE_SOLVE;
         d.max_models = b->max_models_each;
         d.models_cap = b->caps[i];
@@ -1136,7 +1149,13 @@ int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each,
     b->max_models_each = max_models_each;
     b->caps.resize(n);
     for (int32_t i = 0; i < n; i++) b->caps[i] = models_cap ? models_cap[i] : 0;
-    for (int32_t i = 0; i < n; i++) b->units |= progs[i]->D1[0].frontier == 2u;
+    // an explicit configuration keeps the programs' own choice of frontier;
+    // the autotuner tries both where the lists exist
+    bool lists = false;
+    for (int32_t i = 0; i < n; i++) {
+        b->units |= progs[i]->D1[0].frontier == 2u;
+        lists |= progs[i]->batch_units.built;
+    }
     auto bail = [&](int rc) { asp_batch_free(b); return rc; };
     // model buffers of every program
     for (int32_t i = 0; i < n; i++) {
@@ -1176,12 +1195,20 @@ int asp_batch_create(int32_t n, asp_prog *const *progs, int64_t max_models_each,
         const size_t S = std::min<size_t>((size_t)n, 256);
         std::vector<uint32_t> sample(S);
         for (size_t k = 0; k < S; k++) sample[k] = order[k * (size_t)n / S];
+        // schedules: the two kernel configurations, each with full sweeps
+        // and (where the programs have unit lists) with the unit frontier
         double best = -1.0;
-        for (int c = 0; c < 2; c++) {
-            b->trial_ns[c] = batch_trial(b, c, sample);
-            if (b->trial_ns[c] >= 0.0 && (best < 0.0 || b->trial_ns[c] < best)) { best = b->trial_ns[c]; chosen = c; }
+        bool best_units = false;
+        for (int u = 0; u < (lists ? 2 : 1); u++) {
+            b->units = u == 1;
+            for (int c = 0; c < 2; c++) {
+                const double t = batch_trial(b, c, sample);
+                b->trial_ns[c + 2 * u] = t;
+                if (t >= 0.0 && (best < 0.0 || t < best)) { best = t; chosen = c; best_units = u == 1; }
+            }
         }
         if (best < 0.0) return bail(fail(ASP_E_CUDA, "no batch configuration can run"));
+        b->units = best_units;
     }
     int rc = batch_prepare(b, chosen, order);
     if (rc != ASP_OK) return bail(rc);
@@ -1231,13 +1258,16 @@ int asp_batch_run(asp_batch *b, int32_t *statuses, int64_t *n_models, uint64_t *
     return ASP_OK;
 }
 
-int asp_batch_info(const asp_batch *b, int32_t *config, int32_t *block_threads, int32_t *grid, double *trial_ns)
+int asp_batch_info(const asp_batch *b, int32_t *config, int32_t *block_threads, int32_t *grid, int32_t *frontier,
+                   double *trial_ns)
 {
     if (!b) return fail(ASP_E_ARG, "bad argument");
     if (config) *config = b->config;
     if (block_threads) *block_threads = batch_threads(b->config);
     if (grid) *grid = b->grid;
-    if (trial_ns) { trial_ns[0] = b->trial_ns[0]; trial_ns[1] = b->trial_ns[1]; }
+    if (frontier) *frontier = b->units ? ASP_FRONTIER_UNITS : ASP_FRONTIER_FULL;
+    if (trial_ns)
+        for (int i = 0; i < 4; i++) trial_ns[i] = b->trial_ns[i];
     return ASP_OK;
 }
 

@@ -151,7 +151,7 @@ def _oracle_on_all_cores(progs, budget_s):
 def test_batch_4096_statuses_equal_the_oracle(gpu, rules_per_atom, conflicts, oracle_s):
     progs = batch_programs(4096, rules_per_atom=rules_per_atom, config_id=4)
     want = _oracle_on_all_cores(progs, oracle_s)
-    P = [gpu.Program(p, conflict_budget=conflicts, time_budget_ms=20_000, deps_levels=1024,
+    P = [gpu.Program(p, conflict_budget=conflicts, time_budget_ms=int(1000 * oracle_s) + 3000, deps_levels=1024,
                      learned_capacity=1 << 20) for p in progs]
     st, nm, models = gpu.solve_batch(P, max_models_each=1, cap_each=1)
     decided = (st == gpu.SAT) | (st == gpu.UNSAT)
