@@ -63,6 +63,12 @@ extern "C" {
 #define ASP_HEUR_JW 4         /* Jeroslow-Wang (Section 4): sum of 2^-|delta| over the nogoods
                                  delta holding Fb_r or F head(r), the clauses the decision
                                  Tb_r satisfies (computed at load) */
+#define ASP_HEUR_VSIDS 5      /* decaying activity (Section 4 names activity among the decision
+                                 heuristics; this form is not the paper's): each variable of a
+                                 learned nogood bumps the rules it stands for (b_r, t_r, n_r its
+                                 rule; an atom the rules with it as head) by an increment that
+                                 grows by 1/0.95 per learned nogood; ties go to the head's
+                                 occurrences, then to the lowest rule */
 
 /* Shared-memory assignment view of each CTA during the propagate-and-check
  * sweep (Section 4.1; the layout is this implementation's, not the paper's).

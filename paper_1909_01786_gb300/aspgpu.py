@@ -17,7 +17,7 @@ from . import build as _build
 
 ASP_OK, ASP_E_CAPACITY = 0, -5
 MLP_FEATURES, MLP_PARAMS = 16, 1153
-HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED, HEUR_LEARNED_STATIC, HEUR_JW = 0, 1, 2, 3, 4
+HEUR_OCCURRENCE, HEUR_ACTIVITY, HEUR_LEARNED, HEUR_LEARNED_STATIC, HEUR_JW, HEUR_VSIDS = 0, 1, 2, 3, 4, 5
 SAT, UNSAT, UNKNOWN = 10, 20, 0
 VIEW_AUTO, VIEW_PLAIN, VIEW_PACKED, VIEW_BYTES = 0, 1, 2, 3
 LEARN_FWD, LEARN_RES = 0, 1

@@ -594,7 +594,7 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
     D.WW = WW;
     D.Wlevels = WW * 64u;
     D.heuristic = (uint32_t)std::max(0, p->opt.heuristic);
-    if (D.heuristic > 4) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
+    if (D.heuristic > 5) { delete p; return fail(ASP_E_ARG, "unknown heuristic"); }
     if (p->opt.learning < 0 || p->opt.learning > 1) { delete p; return fail(ASP_E_ARG, "unknown learning"); }
     D.learning = (uint32_t)p->opt.learning;
     if (p->opt.backjump < 0 || p->opt.backjump > 1 || p->opt.restart_conflicts < 0) {
@@ -685,7 +685,13 @@ int asp_load_ground(int32_t n_atoms, int32_t n_rules, const int32_t *head,
         if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "watches");
     }
-    D.act = (uint32_t *)alloc((size_t)D.J * 4 + 4);
+    D.act = (uint32_t *)alloc((size_t)D.J * 4 + 8);
+    if (rc == ASP_OK && D.heuristic == 5) {
+        std::vector<uint32_t> hf((size_t)D.na + 1, 0u);
+        for (uint32_t j = 0; j < D.J; j++) hf[(size_t)H.rule_head[j] + 1]++;
+        for (uint32_t a = 0; a < D.na; a++) hf[a + 1] += hf[a];
+        D.head_first = upload(p, hf, rc);
+    }
     D.asg = (uint32_t *)alloc((size_t)D.asg_words * 4 + 4);
     D.dl = (int32_t *)alloc((size_t)D.nv * 4 + 4);
     D.reason = (uint32_t *)alloc((size_t)D.nv * 4 + 4);
@@ -767,7 +773,7 @@ static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t m
         e = cudaMemsetAsync(D.asg, 0, (size_t)D.asg_words * 4 + 4, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(D.dl, 0, (size_t)D.nv * 4 + 4, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(D.act, 0, (size_t)D.J * 4 + 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.act, 0, (size_t)D.J * 4 + 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.stats, 0, sizeof(DevStats), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.bar, 0, sizeof(Barrier), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.level_start, 0, ((size_t)D.J + 4) * 4, st);

@@ -154,7 +154,10 @@ struct Dev {
     uint2 *nwatch;
     const int32_t *rule_head;
     const uint32_t *rpos_off, *rpos, *rneg_off, *rneg, *score;
+    // per rule: conflicts it took part in (heuristic 1), or its VSIDS-style
+    // activity as a float with the increment after the J rules (heuristic 5)
     uint32_t *act;
+    const uint32_t *head_first;   // heuristic 5: rules of atom p are [head_first[p], head_first[p+1])
     // learned decision heuristic (heuristic 2): static rule features
     // [J][8], MLP weights (bf16 bits, MLP_PARAMS), decision trace
     const float *rfeat;

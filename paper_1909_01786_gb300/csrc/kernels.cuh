@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *d
         // reset this program's search state
         for (uint32_t w = threadIdx.x; w <= D.asg_words; w += blockDim.x) D.asg[w] = 0u;
         for (uint32_t v = threadIdx.x; v < D.nv; v += blockDim.x) D.dl[v] = 0;
-        for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) D.act[j] = 0u;
+        for (uint32_t j = threadIdx.x; j <= D.J; j += blockDim.x) D.act[j] = 0u;
         if (D.frontier >= 2u)
             for (uint32_t w = threadIdx.x; w < 2u * D.dirty_words; w += blockDim.x) D.dirty[w] = 0u;
         if (threadIdx.x == 0) {

@@ -564,36 +564,6 @@ __device__ __forceinline__ void lane_deps(const SweepCtx &X, const uint32_t (&va
     }
 }
 
-// Dependency bitmap of x (claimed by one lane) computed by the whole warp:
-// every lane loads the levels of the nogood's other variables (the same
-// addresses, one transaction each) and ORs the bitmap words w = lane,
-// lane + 32, ... over those with level > 1 (Section 4.2, mk_dl_bitmap), so a
-// claim costs two dependent loads whatever the bitmap width.  All 32 lanes
-// call it with the same arguments.
-template <int L>
-__device__ __forceinline__ void warp_deps(const SweepCtx &X, const uint32_t (&var)[L], uint32_t x)
-{
-    const Dev &D = *X.D;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t nw = deps_words(D, X.cdl);
-    const uint32_t dbit = level_bit(D, X.cdl);
-    int32_t Lu[L];
-    bool has_dec = false;
-#pragma unroll
-    for (int q = 0; q < L; q++) {
-        const uint32_t u = var[q];
-        has_dec |= u != x && u == X.dec_v;
-        Lu[q] = (u != x && u != X.dec_v) ? __ldcg(D.dl + u) : 0;
-    }
-    for (uint32_t w = lane; w < nw; w += 32u) {
-        unsigned long long acc = (has_dec && w == (dbit >> 6)) ? (1ull << (dbit & 63u)) : 0ull;
-#pragma unroll
-        for (int q = 0; q < L; q++)
-            if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= __ldcg(D.deps + (size_t)var[q] * D.WW + w);
-        D.deps[(size_t)x * D.WW + w] = acc;
-    }
-}
-
 // Dependency bitmaps (Section 4.2, mk_dl_bitmap) -- and, with the frontier
 // by units, the unit marks -- of every claim of a group of 32 nogoods at
 // once: the claims take equal shares of the warp's lanes (32 / p2 lanes
@@ -653,8 +623,11 @@ __device__ __forceinline__ bool group_claims(const SweepCtx &X, bool won, const 
     return true;
 }
 
-// warp_deps for a nogood of L <= BUCKET_MAX literals known at run time
-// (var[q] for q < L).  All 32 lanes call it with the same arguments.
+// Dependency bitmap of x (claimed by one lane) computed by the whole warp,
+// for a nogood of L <= BUCKET_MAX literals known at run time (var[q] for
+// q < L): every lane loads the levels of the nogood's other variables and
+// ORs the bitmap words w = lane, lane + 32, ... over those with level > 1
+// (Section 4.2, mk_dl_bitmap).  All 32 lanes call it with the same arguments.
 __device__ __forceinline__ void warp_deps_dyn(const SweepCtx &X, const uint32_t (&var)[BUCKET_MAX], uint32_t L,
                                               uint32_t x)
 {
@@ -1408,7 +1381,9 @@ __device__ __forceinline__ uint32_t float_key(float f)
 
 // Decision (Section 2 / Section 4): among rules whose head is unassigned,
 // with t_r true, n_r not false and b_r unassigned (applicable), pick the
-// highest score, ties to the lowest rule index.
+// highest score, ties to the lowest rule index.  Every key is
+// (score << 32) | (0xFFFFFFFF - j): the decision phase recovers the rule j
+// from the low word.
 __device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, uint32_t gtid, uint32_t nthreads,
                                        uint32_t cdl, uint32_t tend)
 {
@@ -1453,6 +1428,16 @@ __device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, ui
                 const float z = mlp_score(S.mlp, x);
                 const float log_p = z >= 0.0f ? -log1pf(__expf(-z)) : z - log1pf(__expf(z));
                 key = ((unsigned long long)float_key(x[0] + log_p) << 32) | (0xFFFFFFFFull - j);
+            } else if (D.heuristic == 5) {
+                // activity, plus the head's occurrences times a millionth of
+                // the current increment (at most 4095 of them: less than one
+                // bump) to order rules of equal activity; ties to the lowest
+                // rule.  The low word stays ~j, which the decision phase decodes.
+                const float *vact = reinterpret_cast<const float *>(D.act);
+                const float a = __ldcg(vact + j);
+                const float occ = (float)min(__ldg(D.score + j), 4095u);
+                const float sc = a + occ * (__ldcg(vact + D.J) * 1e-6f);
+                key = ((unsigned long long)float_key(sc) << 32) | (0xFFFFFFFFull - j);
             } else {
                 unsigned long long sc = __ldg(D.score + j);
                 if (D.heuristic == 1) sc += (unsigned long long)__ldcg(D.act + j) * 8ull;
@@ -1471,6 +1456,41 @@ __device__ __forceinline__ void decide(const Dev &D, const Smem &S, Acc *acc, ui
         x = shfl_max_u64(x);
         if (lane == 0 && x) atomicMax(&acc->dkey, x);
     }
+}
+
+// VSIDS-style activity (heuristic 5, not in the paper; the paper's
+// Decision kernel names activity among its heuristics): every variable of a
+// learned nogood bumps the rules it stands for -- b_j, t_j or n_j rule j, an
+// atom the rules with it as head -- by the current increment, stored as a
+// float after the J activities.  The increment grows by 1/0.95 per learned
+// nogood (vsids_decay), so earlier bumps count less and less.
+__device__ __forceinline__ void vsids_bump(const Dev &D, uint32_t var, float inc)
+{
+    float *vact = reinterpret_cast<float *>(D.act);
+    if (var >= D.nv) return;
+    if (var >= D.na) {
+        atomicAdd(vact + (var - D.na) / 3u, inc);
+        return;
+    }
+    for (uint32_t j = __ldg(D.head_first + var); j < __ldg(D.head_first + var + 1u); j++) atomicAdd(vact + j, inc);
+}
+
+// After each analysis (all threads of the analysing CTA): the increment
+// grows by 1/0.95; above 1e20 every activity and the increment are scaled
+// by 1e-20, which keeps their order.
+__device__ __forceinline__ void vsids_decay(const Dev &D)
+{
+    __shared__ int s_rescale;
+    float *vact = reinterpret_cast<float *>(D.act);
+    cta_sync();
+    if (threadIdx.x == 0) {
+        float inc = __ldcg(vact + D.J) * (1.0f / 0.95f);
+        s_rescale = inc > 1e20f;
+        vact[D.J] = s_rescale ? inc * 1e-20f : inc;
+    }
+    cta_sync();
+    if (s_rescale)
+        for (uint32_t j = threadIdx.x; j < D.J; j += blockDim.x) vact[j] *= 1e-20f;
 }
 
 // fwd-learning (Algorithm 4) on CTA 0: OR the dependency bitmaps of the
@@ -1575,6 +1595,12 @@ __device__ __forceinline__ void analyze(const Dev &D, const Smem &S, uint32_t g,
         }
     }
     cta_sync();
+    if (D.heuristic == 5 && !S.misc[0]) {
+        const float inc = __ldcg(reinterpret_cast<const float *>(D.act) + D.J);
+        for (uint32_t q = tid; q < S.misc[2] && lfill + q < D.lits_cap; q += nt)
+            vsids_bump(D, (__ldcg(D.lits + lfill + q) & ~END_BIT) >> 1, inc);
+        vsids_decay(D);
+    }
 }
 
 // Register learned nogood number i (its first literal at `id`, len
@@ -1827,8 +1853,14 @@ __device__ __forceinline__ void res_analyze(const Dev &D, const Smem &S, uint32_
                 if (bv >= D.na && (bv - D.na) % 3u == 0u) atomicAdd(D.act + (bv - D.na) / 3u, 1u);
             }
         }
+        if (!R.err && D.heuristic == 5) {
+            const float inc = __ldcg(reinterpret_cast<const float *>(D.act) + D.J);
+            for (uint32_t q = lane; q < n && lfill + q < D.lits_cap; q += 32u)
+                vsids_bump(D, (__ldcg(D.lits + lfill + q) & ~END_BIT) >> 1, inc);
+        }
     }
     cta_sync();
+    if (D.heuristic == 5 && S.misc[0] == 0u) vsids_decay(D);
 }
 
 __device__ __forceinline__ View make_view(const Dev &D, uint32_t *vbase, uint32_t cta)
@@ -1979,6 +2011,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         switch (C.op) {
         case OP_INIT: {
             SweepCtx X{&D, V, fresh_cur, 1u, tend, acc, true, false, 0xFFFFFFFFu, cta, rank >> 5, size >> 5};
+            if (leader && D.heuristic == 5) reinterpret_cast<float *>(D.act)[D.J] = 1.0f;   // the first increment
             for (uint32_t i = gtid; i < D.n_units; i += nthreads) {
                 uint32_t id = D.units_base + i;
                 uint32_t l = __ldg(D.lits + id) & ~END_BIT;
@@ -2156,6 +2189,12 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
                 break;
             }
             const uint32_t j = 0xFFFFFFFFu - (uint32_t)(A.dkey & 0xFFFFFFFFull);
+            if (j >= D.J || C.cdl + 1u > D.J + 1u) {
+                // a decision key that names no rule: stop with an error
+                // rather than write outside the arrays
+                if (leader) { N.op = OP_DONE; N.err = -6; N.status = 0; }
+                break;
+            }
             const uint32_t L = C.cdl + 1u;
             const uint32_t bv = D.na + 3u * j;
             if (leader) {

@@ -1,11 +1,14 @@
-"""Compact completion and the Jeroslow-Wang decision score (needs a GB300).
+"""Compact completion, the Jeroslow-Wang score and the decaying activity
+(VSIDS-style) decision heuristic (needs a GB300).
 
 Compact completion leaves out, for empty positive or negative bodies, the
 nogoods that the units {Ft_r} / {Fn_r} settle at the root: the library's
 nogood and literal counts equal the oracle's compact completion, unit
 propagation reaches the oracle's closure, and the answer sets are unchanged.
-The Jeroslow-Wang score (Section 4 names it among the decision heuristics)
-only orders decisions: answers equal the oracle's."""
+The Jeroslow-Wang score and the decaying activity (Section 4 names
+Jeroslow-Wang and activity among the decision heuristics) only order
+decisions: answers equal the oracle's, under fwd-learning and first-UIP
+resolution learning alike."""
 import json
 import os
 
@@ -73,7 +76,7 @@ def test_compact_closure_equals_the_oracle(gpu, seed):
             assert (clo == oclo[perm]).all()
 
 
-@pytest.mark.parametrize("heuristic,compact", [(0, True), (4, False), (4, True)])
+@pytest.mark.parametrize("heuristic,compact", [(0, True), (4, False), (4, True), (5, False)])
 def test_tiny_programs_enumerate_the_brute_force(gpu, heuristic, compact):
     golden = _golden()
     for i in range(0, 1000, 7):
@@ -83,7 +86,7 @@ def test_tiny_programs_enumerate_the_brute_force(gpu, heuristic, compact):
         assert status == (gpu.SAT if golden[i] else gpu.UNSAT)
 
 
-@pytest.mark.parametrize("heuristic,compact", [(4, False), (4, True), (1, True)])
+@pytest.mark.parametrize("heuristic,compact", [(4, False), (4, True), (1, True), (5, False)])
 @pytest.mark.parametrize("seed", range(5))
 def test_medium_programs_agree_with_the_oracle(gpu, heuristic, compact, seed):
     prog = random_program(300 + 400 * seed, 900 + 800 * seed, program_seed(622, seed))
@@ -100,7 +103,7 @@ def test_colouring_enumeration_under_jw_and_compact(gpu):
     prog = coloring_program(40, 4.5, seed_index=7)
     ost, om, _ = oracle.cdnl(prog, time_budget_s=120)
     assert ost == oracle.SAT
-    for heuristic, compact in ((4, False), (4, True), (0, True)):
+    for heuristic, compact in ((4, False), (4, True), (0, True), (5, False)):
         st, models, cnt = gpu.Program(prog, heuristic=heuristic, compact=compact,
                                       time_budget_ms=120_000).solve(0, cap=1 << 12)
         assert _sets(models) == _sets(om) and cnt == len(om), (heuristic, compact)
@@ -113,3 +116,25 @@ def test_compact_batched(gpu):
     st, nm, models = gpu.solve_batch(P, max_models_each=0, cap_each=64)
     for k, i in enumerate(idx):
         assert _masks(models[k], 20) == golden[i] and nm[k] == len(golden[i]), i
+
+
+@pytest.mark.parametrize("learning,restarts", [(0, 0), (1, 0), (1, 16)])
+@pytest.mark.parametrize("seed", range(4))
+def test_vsids_search_answers(gpu, learning, restarts, seed):
+    prog = random_program(500 + 300 * seed, 1100 + 600 * seed, program_seed(623, seed))
+    ost, _, _ = oracle.cdnl(prog, max_models=1, time_budget_s=60)
+    assert ost in (oracle.SAT, oracle.UNSAT)
+    P = gpu.Program(prog, heuristic=gpu.HEUR_VSIDS, learning=learning, restart_conflicts=restarts,
+                    time_budget_ms=60_000)
+    st, models, _ = P.solve(1, cap=1)
+    assert st == (gpu.SAT if ost == oracle.SAT else gpu.UNSAT)
+    for m in models:
+        assert oracle.is_answer_set(prog, m)
+
+
+def test_vsids_colouring_enumeration_with_resolution_and_restarts(gpu):
+    prog = coloring_program(40, 4.5, seed_index=7)
+    ost, om, _ = oracle.cdnl(prog, time_budget_s=120)
+    st, models, cnt = gpu.Program(prog, heuristic=gpu.HEUR_VSIDS, learning=gpu.LEARN_RES, restart_conflicts=8,
+                                  time_budget_ms=120_000).solve(0, cap=1 << 12)
+    assert _sets(models) == _sets(om) and cnt == len(om)
