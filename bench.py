@@ -620,7 +620,9 @@ def _big_store(a, aspgpu, torch, dev, peak):
     out = {"workload": f"random program, {a.big_atoms // 1000}k atoms, {4 * a.big_atoms // 1000}k rules, "
                        f"body 1-4, negation 0.5; store {st['store_bytes'] / 1e6:.0f} MB (> 126 MB L2)",
            "store_bytes": st["store_bytes"], "nogoods": st["n_nogoods"], "literals": st["n_literals"],
-           "sweep": {"ms_per_pass": per_pass, "bytes_per_pass": sweep_bytes, "achieved_gbs": sw_gbs,
+           "sweep": {"ms_per_pass": per_pass, "ms_one_pass_launch": t1, "ms_17_pass_launch": tk,
+                     "view_mode": {1: "plain 2-bit", 2: "packed 2-bit", 3: "bytes"}.get(st["view_mode"]),
+                     "bytes_per_pass": sweep_bytes, "achieved_gbs": sw_gbs,
                      "frac_of_hbm": sw_gbs / peak if peak else None,
                      "note": "standalone sweep_kernel, (t(17 passes) - t(1 pass)) / 16, CUDA events"},
            "solver": {"status": int(status), "conflict_budget": a.big_conflicts, "device_ms": dev_ms,

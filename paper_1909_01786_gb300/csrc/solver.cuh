@@ -514,12 +514,17 @@ __device__ __forceinline__ void warp_or_deps(const SweepCtx &X, bool has, uint32
     const uint32_t L = X.cdl;
     const uint32_t nw = deps_words(D, L);
     const bool is_dec = has && u == X.dec_v;
+    // a decision's bitmap is the bit of its own level: with the level, the
+    // reason tells whether the bitmap words need loading at all (a learned
+    // nogood of fwd-learning holds decisions only)
     int32_t Lu = !has ? 0 : is_dec ? (int32_t)L : __ldcg(D.dl + u);
+    const uint32_t ru = (has && !is_dec) ? __ldcg(D.reason + u) : 0u;
     uint32_t nwu = (has && Lu > 1) ? deps_words(D, (uint32_t)Lu) : 0u;
-    const uint32_t dbit = level_bit(D, L);
+    const bool dec = is_dec || (has && Lu > 1 && ru == R_DECISION);
+    const uint32_t dbit = level_bit(D, dec ? (uint32_t)Lu : L);
     for (uint32_t w = 0; w < nw; w++) {
         unsigned long long c = w >= nwu ? 0ull
-                             : is_dec ? (w == (dbit >> 6) ? (1ull << (dbit & 63u)) : 0ull)
+                             : dec ? (w == (dbit >> 6) ? (1ull << (dbit & 63u)) : 0ull)
                              : __ldcg(D.deps + (size_t)u * D.WW + w);
         unsigned lo = __reduce_or_sync(FULL_MASK, (unsigned)c);
         unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(c >> 32));
@@ -592,6 +597,16 @@ __device__ __forceinline__ bool group_claims(const SweepCtx &X, bool won, const 
     for (int q = 0; q < L; q++) var[q] = X.V.var(__shfl_sync(FULL_MASK, tl[q], src) >> 2);
     const uint32_t xs = __shfl_sync(FULL_MASK, x, src);
     if (c >= nc) return true;
+    // unit marks: the bounds of the claim's unit list load with the levels,
+    // and its first entry for this lane with the bitmap words, so the marks
+    // add no dependent load to the claim
+    uint32_t o0 = 0u, o1 = 0u;
+    if constexpr (MARK) {
+        if (X.dmark) {
+            o0 = __ldg(D.occ_uoff + xs);
+            o1 = __ldg(D.occ_uoff + xs + 1u);
+        }
+    }
     if (X.cdl > 1u) {
         const uint32_t nw = deps_words(D, X.cdl);
         const uint32_t dbit = level_bit(D, X.cdl);
@@ -603,6 +618,10 @@ __device__ __forceinline__ bool group_claims(const SweepCtx &X, bool won, const 
             has_dec |= u != xs && u == X.dec_v;
             Lu[q] = (u != xs && u != X.dec_v) ? __ldcg(D.dl + u) : 0;
         }
+        uint32_t first = 0xFFFFFFFFu;
+        if constexpr (MARK) {
+            if (o0 + sub < o1) first = __ldg(D.occ_unit + o0 + sub);
+        }
         for (uint32_t w = sub; w < nw; w += gs) {
             unsigned long long acc = (has_dec && w == (dbit >> 6)) ? (1ull << (dbit & 63u)) : 0ull;
 #pragma unroll
@@ -610,14 +629,19 @@ __device__ __forceinline__ bool group_claims(const SweepCtx &X, bool won, const 
                 if (Lu[q] > 1 && 64u * w < (uint32_t)Lu[q]) acc |= __ldcg(D.deps + (size_t)var[q] * D.WW + w);
             D.deps[(size_t)xs * D.WW + w] = acc;
         }
-    }
-    if constexpr (MARK) {
-        if (X.dmark) {
-            const uint32_t o0 = __ldg(D.occ_uoff + xs), o1 = __ldg(D.occ_uoff + xs + 1u);
-            for (uint32_t o = o0 + sub; o < o1; o += gs) {
+        if constexpr (MARK) {
+            if (first != 0xFFFFFFFFu) atomicOr(X.dmark + (first >> 5), 1u << (first & 31u));
+            for (uint32_t o = o0 + sub + gs; o < o1; o += gs) {
                 const uint32_t u = __ldg(D.occ_unit + o);
                 atomicOr(X.dmark + (u >> 5), 1u << (u & 31u));
             }
+        }
+        return true;
+    }
+    if constexpr (MARK) {
+        for (uint32_t o = o0 + sub; o < o1; o += gs) {
+            const uint32_t u = __ldg(D.occ_unit + o);
+            atomicOr(X.dmark + (u >> 5), 1u << (u & 31u));
         }
     }
     return true;
