@@ -257,7 +257,8 @@ def run_ours(a, rank, world, local_rank):
     totals = dict(literal_checks=0, nogood_visits=0, propagations=0, decisions=0, conflicts=0, rounds=0,
                   max_level=0, learned=0, learned_literals=0,
                   ns_total=0, ns_sweep=0, ns_analysis=0, ns_decision=0, ns_stability=0,
-                  ns_buckets=0, ns_learned=0, ns_barrier=0, ns_slowest_cta=0, ns_slowest_sweep=0)
+                  ns_buckets=0, ns_learned=0, ns_barrier=0, ns_slowest_cta=0, ns_slowest_sweep=0,
+                  ns_slowest_long=0, ns_slowest_buckets=0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     statuses = []
     barrier()
@@ -384,7 +385,8 @@ def run_ours(a, rank, world, local_rank):
                        "device_ns": {k: totals[k] for k in ("ns_total", "ns_sweep", "ns_analysis",
                                                            "ns_decision", "ns_stability", "ns_buckets",
                                                            "ns_learned", "ns_barrier", "ns_slowest_cta",
-                                                           "ns_slowest_sweep")}},
+                                                           "ns_slowest_sweep", "ns_slowest_long",
+                                                           "ns_slowest_buckets")}},
             "solver_src_sha": sha,
         }
         out["work_vs_oracle"] = _work_ratios(out)
@@ -452,7 +454,8 @@ def _frontiers(a, aspgpu, prog):
                      "nogood_visits_per_round": s["nogood_visits"] / rounds,
                      "literal_checks_per_s": s["literal_checks"] / sec,
                      "us_per_round_split": {k: s[k] / rounds / 1e3 for k in (
-                         "ns_slowest_cta", "ns_slowest_sweep", "ns_buckets", "ns_learned", "ns_barrier")}}
+                         "ns_slowest_cta", "ns_slowest_sweep", "ns_slowest_long", "ns_slowest_buckets",
+                         "ns_buckets", "ns_learned", "ns_barrier")}}
         P.close()
     full = out["full"]["decisions_per_s"]
     for v in out.values():

@@ -199,6 +199,9 @@ typedef struct {
                                                    and learned ones every sweep, the bucket
                                                    ones in full sweeps; frontier rounds'
                                                    nogoods are not counted) */
+    int64_t ns_slowest_long, ns_slowest_buckets; /* sums over sweeps of the slowest warp's time
+                                                   (any CTA) on long and learned nogoods, and
+                                                   on bucket units */
 } asp_stats_t;
 
 /* Default options (all zero except as documented above). */

@@ -55,7 +55,7 @@ class Stats(C.Structure):
         "learned_literals", "loop_nogoods", "models", "max_level", "ns_total",
         "ns_sweep", "ns_analysis", "ns_decision", "ns_stability", "ns_buckets", "ns_learned",
         "ns_barrier", "view_mode", "batch_view_mode", "ns_slowest_cta", "ns_slowest_sweep",
-        "restarts", "conflict_rounds", "nogood_visits")]
+        "restarts", "conflict_rounds", "nogood_visits", "ns_slowest_long", "ns_slowest_buckets")]
 
 
 EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_async", "asp_solve_batch",

@@ -788,7 +788,7 @@ static int reset_state(asp_prog *p, uint32_t mode, int64_t max_models, int64_t m
     ctl[0].lfill = D.lits_static;
     for (int i = 0; i < 4; i++) {
         acc[i].ckey = NO_KEY; acc[i].cslot[0] = acc[i].cslot[1] = acc[i].cslot[2] = NO_KEY; acc[i].dkey = 0; acc[i].nclaim = 0; acc[i].flag = 0;
-        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0; acc[i].visits = 0; acc[i].tbusy = 0; acc[i].tsweep = 0;
+        acc[i].minU = 0xFFFFFFFFu; acc[i].nlits = 0; acc[i].checks = 0; acc[i].visits = 0; acc[i].tbusy = 0; acc[i].tsweep = 0; acc[i].tlong = 0; acc[i].tbuck = 0;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.acc, acc, sizeof(acc), cudaMemcpyHostToDevice, st);
@@ -819,6 +819,7 @@ static void fill_stats(const asp_prog *p, const DevStats &s, asp_stats_t &o)
     o.ns_buckets = (int64_t)s.ns_buckets; o.ns_learned = (int64_t)s.ns_learned; o.ns_barrier = (int64_t)s.ns_barrier;
     o.view_mode = D.view_mode; o.batch_view_mode = p->D1[0].view_mode;
     o.ns_slowest_cta = (int64_t)s.ns_slowest; o.ns_slowest_sweep = (int64_t)s.ns_slowest_sweep;
+    o.ns_slowest_long = (int64_t)s.ns_slowest_long; o.ns_slowest_buckets = (int64_t)s.ns_slowest_buckets;
     o.restarts = (int64_t)s.restarts; o.conflict_rounds = (int64_t)s.conflict_rounds;
     o.nogood_visits = (int64_t)s.visits;
 }
@@ -954,7 +955,7 @@ int asp_sweep(asp_prog *p, int32_t passes)
     Acc a;
     a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY;
     a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.visits = 0;
-    a.tbusy = 0; a.tsweep = 0;
+    a.tbusy = 0; a.tsweep = 0; a.tlong = 0; a.tbuck = 0;
     cudaError_t e = cudaMemcpyAsync(p->d_sweep_acc, &a, sizeof(a), cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep reset");
     e = launch_sweep(p->D, p->d_sweep_acc, p->grid, p->block, p->smem, p->stream, (uint32_t)passes);

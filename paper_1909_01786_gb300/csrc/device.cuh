@@ -81,6 +81,8 @@ struct Acc {              // per-phase accumulators, indexed by phase % 4
     unsigned long long visits;  // bucket nogoods classified by unit frontiers
     unsigned long long tbusy;   // max over CTAs of the time from phase start to barrier arrival
     unsigned long long tsweep;  // max over CTAs of the time in the sweep
+    unsigned long long tlong;   // max over warps of the sweep's long and learned nogoods
+    unsigned long long tbuck;   // max over warps of the sweep's bucket units
 };
 
 struct DevStats {
@@ -102,6 +104,9 @@ struct DevStats {
     // the conflict round included), learned nogood id and length, backjump
     // target, and the level the nogood was resolved at (0 for fwd-learning)
     unsigned long long dbg_conf, dbg_tend, dbg_lfill, dbg_len, dbg_target, dbg_level;
+    // sums over phases of the slowest warp's time on long and learned
+    // nogoods and on bucket units (any CTA)
+    unsigned long long ns_slowest_long, ns_slowest_buckets;
 };
 
 // Grid barrier: arrivals counted since the solve began (barrier g is

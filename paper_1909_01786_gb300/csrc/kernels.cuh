@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) batch_kernel(const Dev *d
             memset(&c, 0, sizeof(c));
             D.ctl[1] = c;
             Acc a;
-            a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.visits = 0; a.tbusy = 0; a.tsweep = 0;
+            a.ckey = NO_KEY; a.cslot[0] = a.cslot[1] = a.cslot[2] = NO_KEY; a.dkey = 0; a.nclaim = 0; a.flag = 0; a.minU = 0xFFFFFFFFu; a.nlits = 0; a.checks = 0; a.visits = 0; a.tbusy = 0; a.tsweep = 0; a.tlong = 0; a.tbuck = 0;
             for (int i = 0; i < 4; i++) D.acc[i] = a;
             memset(D.stats, 0, sizeof(DevStats));
             memset(D.bar, 0, sizeof(Barrier));   // unused here, read by the final error check

@@ -349,6 +349,8 @@ __shared__ unsigned int s_unit, s_unit2[2];
 // CTA 0, thread 0: time in the sweeps on long and learned nogoods and on
 // the buckets
 __shared__ unsigned long long s_tlearned, s_tbuckets;
+// the same two parts, max over the CTA's warps in the current sweep
+__shared__ unsigned long long s_wmax[2];
 // frontier by units (single-program solver only): this round's queue of the
 // CTA's bucket units (local unit indices) and its length
 constexpr uint32_t DQ_CAP = 1024;
@@ -759,6 +761,100 @@ __device__ __forceinline__ uint32_t tlit_count(const View &V, uint32_t tl)
     return __byte_perm(0x01100001u, 0u, (tlit_val<BYTES>(V, tl) ^ tl) & 3u);
 }
 
+// a if p, else b, as a predicated select (the group loop below picks a
+// row of its register arrays with these, which keeps the arrays in
+// registers)
+__device__ __forceinline__ uint32_t sel_if(bool p, uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tselp.b32 %0, %1, %2, q;\n\t}"
+        : "=r"(r) : "r"(a), "r"(b), "r"((uint32_t)p));
+    return r;
+}
+
+// The literals of one lane's nogood of a length-L bucket, as view entries.
+template <int L>
+struct Row { uint32_t q[L]; };
+
+// The claim path of one group of 32 nogoods of bucket L, taken when the
+// count found some lane's nogood unit or violated (cand): that lane
+// classifies it again from the current view (a claim of this CTA may have
+// changed it since the count), reports a violation, or claims the variable
+// of its one unassigned literal; then the group's claims get their
+// dependency bitmaps (and, with the frontier by units, their unit marks),
+// and are published in the view.  All 32 lanes call it.  Returns whether
+// this lane claimed.
+template <int L, bool BYTES, bool MARK>
+__device__ __forceinline__ bool group_claim_path(const SweepCtx &X, const Row<L> &r, uint32_t k, bool cand)
+{
+    const Dev &D = *X.D;
+    bool won = false;
+    uint32_t e = 0, x = 0, valbit = 0;
+    if (cand) {
+        const uint32_t id = bucket_nogood_id((uint32_t)L, k);
+        bool sat = false;
+        uint32_t n_un = 0, ul = 0;
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+            const uint32_t tv = (tlit_val<BYTES>(X.V, r.q[q]) ^ r.q[q]) & 3u;
+            sat |= tv == 2u;
+            if (tv == 0u || tv == 3u) { n_un++; ul = r.q[q]; }
+        }
+        if (!sat && n_un == 0u) {
+            report_conflict(X, id, (uint32_t)L);
+        } else if (!sat && n_un == 1u) {
+            if (!X.do_claim) {
+                atomicAdd(&X.acc->flag, 1u);
+            } else {
+                e = ul >> 2;
+                x = X.V.var(e);
+                valbit = (ul & 1u) ? V_T : V_F;
+                const int rc = claim_var(D.asg, x, valbit, X.fresh);
+                if (rc == 2) report_conflict(X, id, (uint32_t)L);
+                else if (rc == 0) { record_claim(X, x, valbit, id); won = true; }
+            }
+        }
+    }
+    if (L > 8 && won && (MARK || X.cdl > 1u)) {
+        // long buckets (few claims): the claiming lane alone
+        if constexpr (MARK) lane_mark_units(X, x);
+        if (X.cdl > 1u) {
+            uint32_t var[L];
+#pragma unroll
+            for (int q = 0; q < L; q++) var[q] = X.V.var(r.q[q] >> 2);
+            lane_deps<L>(X, var, x);
+        }
+    }
+    if (L <= 8 && (X.cdl > 1u || (MARK && X.dmark))) {
+        // bitmaps (and unit marks) of this group's claims, all at once
+        if (group_claims<L, MARK>(X, won, r.q, x)) {
+            __threadfence_block();
+            __syncwarp();
+        }
+    }
+    if (won) {
+        __threadfence_block();
+        X.V.put(e, valbit);
+    }
+    if constexpr (MARK) {
+        if (X.chain) {
+            // frontier = 3: the CTA's units that hold the claims, for the
+            // next wave (after the claims are in the view)
+            if (L > 8) {
+                if (won) lane_push_units(X, x);
+            } else {
+                unsigned m = __ballot_sync(FULL_MASK, won);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1u;
+                    warp_push_units(X, __shfl_sync(FULL_MASK, x, src));
+                }
+            }
+        }
+    }
+    return won;
+}
+
 // bucket_tasks over the translated copy of the store (view modes PACKED
 // and BYTES): every literal is in the view, one shared-memory load and
 // three integer operations classify it.  Lanes past the end of the range
@@ -785,77 +881,33 @@ __device__ __forceinline__ void bucket_tasks_view(const SweepCtx &X, uint32_t k0
 #pragma unroll
             for (int q = 0; q < L; q++) cnt[t] += tlit_count<BYTES>(X.V, lit[t][q]);
         }
-        bool pub = false;
+        // the groups with a nogood that is violated or unit by the count go
+        // through the claim path, one at a time; the path is written out
+        // once (the group's row is selected into registers), not once per
+        // group, so the loops above stay small enough to stay in the
+        // instruction cache from one round to the next
+        unsigned cm = 0u;
 #pragma unroll
         for (int t = 0; t < U; t++) {
             const uint32_t k = k0 + (uint32_t)t * 32u + lane;
-            bool won = false;
-            uint32_t e = 0, x = 0, valbit = 0;
-            if (k < k1 && (cnt[t] & 0xFFu) <= 1u) {
-                const uint32_t id = bucket_nogood_id((uint32_t)L, k);
-                // violated or unit: classify again from the current view (a
-                // claim of this CTA may have changed it since the count)
-                bool sat = false;
-                uint32_t n_un = 0, ul = 0;
+            if (__any_sync(FULL_MASK, k < k1 && (cnt[t] & 0xFFu) <= 1u)) cm |= 1u << t;
+        }
+        bool pub = false;
+        while (cm) {
+            const int t = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            Row<L> r;
+            uint32_t c = cnt[0];
 #pragma unroll
-                for (int q = 0; q < L; q++) {
-                    const uint32_t tv = (tlit_val<BYTES>(X.V, lit[t][q]) ^ lit[t][q]) & 3u;
-                    sat |= tv == 2u;
-                    if (tv == 0u || tv == 3u) { n_un++; ul = lit[t][q]; }
-                }
-                if (!sat && n_un == 0u) {
-                    report_conflict(X, id, (uint32_t)L);
-                } else if (!sat && n_un == 1u) {
-                    if (!X.do_claim) {
-                        atomicAdd(&X.acc->flag, 1u);
-                    } else {
-                        e = ul >> 2;
-                        x = X.V.var(e);
-                        valbit = (ul & 1u) ? V_T : V_F;
-                        const int r = claim_var(D.asg, x, valbit, X.fresh);
-                        if (r == 2) report_conflict(X, id, (uint32_t)L);
-                        else if (r == 0) { record_claim(X, x, valbit, id); won = true; }
-                    }
-                }
-            }
-            if (L > 8 && won && (MARK || X.cdl > 1u)) {
-                // long buckets (few claims): the claiming lane alone
-                if constexpr (MARK) lane_mark_units(X, x);
-                if (X.cdl > 1u) {
-                    uint32_t var[L];
+            for (int q = 0; q < L; q++) r.q[q] = lit[0][q];
 #pragma unroll
-                    for (int q = 0; q < L; q++) var[q] = X.V.var(lit[t][q] >> 2);
-                    lane_deps<L>(X, var, x);
-                }
+            for (int tt = 1; tt < U; tt++) {
+                c = sel_if(t == tt, cnt[tt], c);
+#pragma unroll
+                for (int q = 0; q < L; q++) r.q[q] = sel_if(t == tt, lit[tt][q], r.q[q]);
             }
-            if (L <= 8 && (X.cdl > 1u || (MARK && X.dmark))) {
-                // bitmaps (and unit marks) of this group's claims, all at once
-                if (group_claims<L, MARK>(X, won, lit[t], x)) {
-                    __threadfence_block();
-                    __syncwarp();
-                }
-            }
-            if (won) {
-                __threadfence_block();
-                X.V.put(e, valbit);
-                pub = true;
-            }
-            if constexpr (MARK) {
-                if (X.chain) {
-                    // frontier = 3: the CTA's units that hold the claims, for
-                    // the next wave (after the claims are in the view)
-                    if (L > 8) {
-                        if (won) lane_push_units(X, x);
-                    } else {
-                        unsigned m = __ballot_sync(FULL_MASK, won);
-                        while (m) {
-                            const int src = __ffs(m) - 1;
-                            m &= m - 1u;
-                            warp_push_units(X, __shfl_sync(FULL_MASK, x, src));
-                        }
-                    }
-                }
-            }
+            const uint32_t k = k0 + (uint32_t)t * 32u + lane;
+            pub |= group_claim_path<L, BYTES, MARK>(X, r, k, k < k1 && (c & 0xFFu) <= 1u);
         }
         if (!X.do_claim || !__any_sync(FULL_MASK, pub)) break;
     }
@@ -1163,7 +1215,8 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     const Dev &D = *X.D;
     const uint32_t lane = threadIdx.x & 31u;
     const bool timer = X.cta == 0 && threadIdx.x == 0 && X.do_claim;
-    const unsigned long long t0 = timer ? globaltimer_ns() : 0ull;
+    const bool wtimer = lane == 0 && X.do_claim;
+    const unsigned long long t0 = wtimer ? globaltimer_ns() : 0ull;
     // Units of work (one bucket, unit_groups(L) consecutive groups of 32
     // nogoods) are taken from a per-CTA counter, bucket after bucket, so
     // every warp runs about the same number of load-gather-classify chains
@@ -1216,7 +1269,7 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
         uint32_t id = i < D.n_long ? __ldg(D.long_ids + i) : __ldcg(D.learned_ids + (i - D.n_long));
         classify_long<(DQ != 0)>(X, id, checks, D.nwatch ? D.nwatch + i : nullptr);
     }
-    const unsigned long long t1 = timer ? globaltimer_ns() : 0ull;
+    const unsigned long long t1 = wtimer ? globaltimer_ns() : 0ull;
     for (;;) {
         uint32_t u = 0;
         if (words && pending) {
@@ -1285,17 +1338,26 @@ __device__ __forceinline__ void sweep(const SweepCtx &X0, uint32_t n_learned, bo
     }
     if (lane == 0 && checks) atomicAdd(&X.acc->checks, checks);
     if (lane == 0 && uvisits) atomicAdd(&X.acc->visits, uvisits);
-    if (timer) {
+    if (wtimer) {
         const unsigned long long t2 = globaltimer_ns();
-        s_tlearned += t1 - t0;
-        s_tbuckets += t2 - t1;
+        if (timer) {
+            s_tlearned += t1 - t0;
+            s_tbuckets += t2 - t1;
+        }
+        atomicMax(&s_wmax[0], t1 - t0);
+        atomicMax(&s_wmax[1], t2 - t1);
     }
     if (X.do_claim) {
         // copy the listed claims to the trail: warp 0 reserves the slots,
         // then every thread copies (no barrier under a data-dependent branch)
         cta_sync();
         const uint32_t n = min(s_ncl, CLAIM_BUF);
-        if (threadIdx.x == 0) { s_unit = 0u; s_nq = 0u; }   // every warp has left the unit queue
+        if (threadIdx.x == 0) {
+            s_unit = 0u; s_nq = 0u;                  // every warp has left the unit queue
+            atomicMax(&X.acc->tlong, s_wmax[0]);
+            atomicMax(&X.acc->tbuck, s_wmax[1]);
+            s_wmax[0] = s_wmax[1] = 0ull;
+        }
         if constexpr (DQ == 1) {
             if (X.chain) {
                 for (uint32_t w = threadIdx.x; w < DQ_BITS / 32u; w += blockDim.x) s_dqbits[w] = 0u;
@@ -1976,17 +2038,18 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
     // leader-only counters (shared memory, not registers of every thread),
     // written to the stats when the search ends
     __shared__ unsigned long long t_start, t_phase, n_conf, n_phases, ns_bar, ns_sw, ns_an, ns_de, ns_st;
-    __shared__ unsigned long long ns_slow, ns_slow_sw, t_cta0;
+    __shared__ unsigned long long ns_slow, ns_slow_sw, ns_slow_long, ns_slow_buck, t_cta0;
     // restarts: learned nogoods since the last restart, restarts so far
     __shared__ uint32_t r_conf, r_idx;
     if (leader) {
         t_start = globaltimer_ns();
         t_phase = t_start;
         n_conf = n_phases = ns_bar = ns_sw = ns_an = ns_de = ns_st = ns_slow = ns_slow_sw = 0ull;
+        ns_slow_long = ns_slow_buck = 0ull;
         r_conf = 0u;
         r_idx = 0u;
     }
-    if (threadIdx.x == 0) { s_tlearned = 0ull; s_tbuckets = 0ull; t_cta0 = globaltimer_ns(); }
+    if (threadIdx.x == 0) { s_tlearned = 0ull; s_tbuckets = 0ull; s_wmax[0] = s_wmax[1] = 0ull; t_cta0 = globaltimer_ns(); }
 
     if (threadIdx.x == 0) ldcg_copy(&sC, D.ctl);
     if (D.heuristic == 2) {
@@ -2015,7 +2078,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         cta_sync();
         const Ctl C = sC;
         const Acc A = sA;
-        if (leader) { ns_slow += A.tbusy; ns_slow_sw += A.tsweep; }
+        if (leader) { ns_slow += A.tbusy; ns_slow_sw += A.tsweep; ns_slow_long += A.tlong; ns_slow_buck += A.tbuck; }
         if (C.op == OP_DONE) break;
         Acc *acc = D.acc + (k & 3u);
         // the next control block, written by the leader only (kept in
@@ -2470,7 +2533,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
             D.ctl[(k + 1u) & 1u] = N;
             Acc z;
             z.ckey = NO_KEY; z.cslot[0] = z.cslot[1] = z.cslot[2] = NO_KEY; z.dkey = 0; z.nclaim = 0; z.flag = 0; z.minU = 0xFFFFFFFFu; z.nlits = 0; z.checks = 0; z.visits = 0;
-            z.tbusy = 0; z.tsweep = 0;
+            z.tbusy = 0; z.tsweep = 0; z.tlong = 0; z.tbuck = 0;
             D.acc[(k + 1u) & 3u] = z;
             // fold long-nogood checks of the previous phase into the stats
             if (A.checks) atomicAdd(&D.stats->checks, A.checks);
@@ -2506,6 +2569,8 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         D.stats->ns_buckets = s_tbuckets;
         D.stats->ns_slowest = ns_slow;
         D.stats->ns_slowest_sweep = ns_slow_sw;
+        D.stats->ns_slowest_long = ns_slow_long;
+        D.stats->ns_slowest_buckets = ns_slow_buck;
         int err = F.err;
         if (__ldcg(&D.bar->err)) err = -6;
         D.result[0] = F.status;
