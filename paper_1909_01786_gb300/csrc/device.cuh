@@ -109,8 +109,9 @@ struct DevStats {
     unsigned long long ns_slowest_long, ns_slowest_buckets;
 };
 
-// Grid barrier: arrivals counted since the solve began (barrier g is
-// complete once count >= (g + 1) * CTAs); err is set by a CTA that gave up
+// Grid barrier: arrivals counted since the launch began (zeroed by the host
+// before each launch; barrier g is complete once count >= (g + 1) * CTAs);
+// err is set by a CTA that gave up
 // waiting; stall is a flag that nothing sets (the test-only stalled CTA
 // waits on it).
 struct Barrier { unsigned long long count; unsigned int err, stall; };

@@ -67,33 +67,33 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// Grid barrier with a bounded wait: returns false (and sets the sticky error
-// flag) if the other CTAs do not arrive within limit_ns (20 s unless a test
-// shortens it), or if another CTA gave up.  One atomic per CTA on a counter
-// that is never reset: the barrier an arrival belongs to is its count
-// divided by the number of CTAs.
-__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks, unsigned long long limit_ns)
+// Grid barrier number gen (0, 1, ... in every CTA) of a launch, with a
+// bounded wait: returns false (and sets the sticky error flag) if the other
+// CTAs do not arrive within limit_ns (20 s unless a test shortens it), or
+// if another CTA gave up.  The host zeroes the counter before each launch,
+// so barrier gen is complete once it reaches (gen + 1) x CTAs; a CTA
+// arrives with a release add that returns nothing (the CTA's writes,
+// ordered before it by the CTA barrier, become visible with it) and waits
+// with acquire loads.
+__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks, unsigned long long limit_ns, uint32_t gen)
 {
     __shared__ int s_ok;
     cta_sync();
     if (threadIdx.x == 0) {
         int ok = 1;
         if (nblocks > 1) {
-            __threadfence();
-            const unsigned long long old = atomicAdd(&b->count, 1ull);
-            const unsigned long long target = (old / nblocks + 1ull) * nblocks;
-            if (old + 1ull != target) {
-                unsigned long long t0 = 0;
-                for (unsigned spins = 1; ld_acquire_u64(&b->count) < target; spins++) {
-                    if ((spins & 255u) == 0u) {
-                        if (ld_acquire_u32(&b->err)) { ok = 0; break; }
-                        const unsigned long long now = globaltimer_ns();
-                        if (t0 == 0) t0 = now;
-                        else if (now - t0 > limit_ns) {
-                            atomicExch(&b->err, 1u);
-                            ok = 0;
-                            break;
-                        }
+            const unsigned long long target = ((unsigned long long)gen + 1ull) * nblocks;
+            asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(&b->count), "l"(1ull) : "memory");
+            unsigned long long t0 = 0;
+            for (unsigned spins = 1; ld_acquire_u64(&b->count) < target; spins++) {
+                if ((spins & 255u) == 0u) {
+                    if (ld_acquire_u32(&b->err)) { ok = 0; break; }
+                    const unsigned long long now = globaltimer_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > limit_ns) {
+                        atomicExch(&b->err, 1u);
+                        ok = 0;
+                        break;
                     }
                 }
             }
@@ -1998,13 +1998,13 @@ __device__ __forceinline__ uint32_t luby(uint32_t i)
 // Phase barrier of the solving group: the whole grid (one program on every
 // SM) or one CTA (one program of a batch).
 template <bool BATCH>
-__device__ __forceinline__ bool group_sync(const Dev &D)
+__device__ __forceinline__ bool group_sync(const Dev &D, uint32_t gen)
 {
     if (BATCH) {
         cta_sync();
         return true;
     }
-    return grid_sync(D.bar, gridDim.x, D.barrier_ns);
+    return grid_sync(D.bar, gridDim.x, D.barrier_ns, gen);
 }
 
 // Test-only failure injection: CTA D.stall_cta (thread 0) waits on a flag
@@ -2551,7 +2551,7 @@ __device__ __forceinline__ void solver_loop(const Dev &D, const Smem &S, const V
         const unsigned long long tb0 = threadIdx.x == 0 ? globaltimer_ns() : 0ull;
         if (threadIdx.x == 0) atomicMax(&acc->tbusy, tb0 - t_cta0);
         if (!BATCH && k == 0 && D.stall_cta != 0xFFFFFFFFu) injected_stall(D);
-        if (!group_sync<BATCH>(D)) break;
+        if (!group_sync<BATCH>(D, k)) break;
         if (threadIdx.x == 0) t_cta0 = globaltimer_ns();
         if (leader) ns_bar += t_cta0 - tb0;
     }
