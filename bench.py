@@ -719,6 +719,13 @@ def _summary(out):
                             g(out, "learned_heuristic", "speedup_static_solved_per_s")],
         "frontier_decisions_per_s": {k: g(out, "frontier_compare", k, "decisions_per_s")
                                      for k in (out.get("frontier_compare") or {})},
+        # literals read per round: every bucket literal (full sweeps, the
+        # headline's count) against those of the nogoods holding a variable
+        # assigned in the previous round (the occurrence-list frontier)
+        "literal_checks_per_round": {"scanned_full_sweeps": g(out, "frontier_compare", "full",
+                                                              "literal_checks_per_round"),
+                                     "necessary_occurrence_lists": g(out, "frontier_compare", "nogoods",
+                                                                     "literal_checks_per_round")},
     }
 
 
