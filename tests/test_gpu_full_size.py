@@ -18,7 +18,10 @@ still computes two outputs exactly, and they are compared here:
   reason's other variables above the root (mk_dl_bitmap); a decision's
   bitmap is its own level.  With the cone checked, the learned nogood must be
   the decision literals of the levels in the OR over the violated nogood,
-  the backjump target h-1, and the nogood unit there."""
+  the backjump target h-1 (the second-highest level under the asserting
+  option), and the nogood unit there; also under the unit frontier;
+- first-UIP resolution learning (Algorithm 3) at the k-th conflict: the
+  learned nogood and target equal the oracle's first_uip on the GPU's state."""
 import numpy as np
 import pytest
 
@@ -153,14 +156,11 @@ def _deps_levels(row, L):
     return frozenset(out)
 
 
-@pytest.mark.parametrize("k", [1, 3, 8])
-def test_fwd_learning_at_full_size(gpu, large, k):
-    prog, comp = large
-    P = gpu.Program(prog, conflict_budget=k, time_budget_ms=60_000)
-    status, _, _ = P.solve(1, cap=1)
+def _check_fwd_conflict(gpu, P, comp, k, asserting=False):
+    """The cone of the last conflict's violated nogood, reason by reason, and
+    the learned nogood and target of Algorithm 4 from it (see the module
+    docstring); returns (cone size, learned length, target)."""
     s = P.stats()
-    if status != gpu.UNKNOWN or s["conflicts"] != k:
-        pytest.skip("search ended before the k-th conflict")
     lc = P.last_conflict()
     assert lc is not None and "learned" in lc
     words = (int(s["max_level"]) + 63) // 64 + 1
@@ -229,8 +229,82 @@ def test_fwd_learning_at_full_size(gpu, large, k):
     got = [int(l) for l in P.nogood(lc["learned"])]
     assert len(got) == lc["length"] == len(set(got))
     assert set(got) == {dec[L] << 1 for L in levels}
-    assert lc["target"] == h - 1
+    if asserting:
+        below = sorted(L for L in levels if L < h)
+        assert lc["target"] == (below[-1] if below else 1)
+    else:
+        assert lc["target"] == h - 1
+    # unit at the target: only the decision of level h is above it
     at_h = [l for l in got if level[l >> 1] > lc["target"]]
     assert at_h == [dec[h] << 1]
-    print(f"k={k}: cone of {checked} variables, learned nogood of {len(got)} decisions, target {h - 1}")
+    return checked, len(got), lc["target"]
+
+
+# (conflict k, options): the benchmark's defaults, then the unit frontier
+# (the fastest propagation-round mode of the benchmark's comparison) and the
+# asserting-level backjump
+FWD_CASES = [(1, {}), (3, {}), (8, {}), (25, {}),
+             (4, {"frontier": 2}), (15, {"frontier": 2}),
+             (6, {"backjump": 1})]
+
+
+@pytest.mark.parametrize("k,opts", FWD_CASES, ids=[f"k{k}-{'-'.join(f'{a}{b}' for a, b in o.items()) or 'default'}"
+                                                   for k, o in FWD_CASES])
+def test_fwd_learning_at_full_size(gpu, large, k, opts):
+    prog, comp = large
+    P = gpu.Program(prog, conflict_budget=k, time_budget_ms=60_000, **opts)
+    status, _, _ = P.solve(1, cap=1)
+    if status != gpu.UNKNOWN or P.stats()["conflicts"] != k:
+        pytest.skip("search ended before the k-th conflict")
+    cone, n, target = _check_fwd_conflict(gpu, P, comp, k, asserting=opts.get("backjump") == 1)
+    print(f"fwd k={k} {opts}: cone of {cone} variables, learned nogood of {n} decisions, target {target}")
+    P.close()
+
+
+@pytest.mark.parametrize("k", [1, 4, 12])
+def test_resolution_learning_at_full_size(gpu, large, k):
+    """First-UIP resolution learning (Algorithm 3, the paper's baseline
+    analysis) at the k-th conflict of the benchmark's search: the learned
+    nogood, its first literal and the target equal the oracle's first_uip run
+    on the GPU's own state (trail order, levels, reasons, violated nogood);
+    the GPU leaves root-level literals out of the nogood."""
+    prog, comp = large
+    P = gpu.Program(prog, learning=gpu.LEARN_RES, conflict_budget=k, time_budget_ms=60_000)
+    status, _, _ = P.solve(1, cap=1)
+    if status != gpu.UNKNOWN or P.stats()["conflicts"] != k:
+        pytest.skip("search ended before the k-th conflict")
+    lc = P.last_conflict()
+    assert lc is not None and "learned" in lc
+    st = P.state()
+    level, reason = st["level"], st["reason"]
+    tl = lc["trail"].astype(np.int64)
+    tv = tl >> 1
+    pos = np.full(P.n_vars, -1, np.int64)
+    pos[tv] = np.arange(tv.shape[0])
+    is_false = np.zeros(P.n_vars, bool)
+    is_false[tv] = (tl & 1) == 1
+    dec = {int(level[v]): int(v) for v in tv[reason[tv] == gpu.R_DECISION].tolist()}
+    learned_ids = {int(i) for i in P.learned_ids()}
+
+    def lits(arr):
+        return [(int(l) >> 1, bool(int(l) & 1)) for l in arr]
+
+    def antecedent(v):
+        r = int(reason[v])
+        if r == gpu.R_DECISION:
+            return None
+        if r == gpu.R_COMPLETE:
+            return [(v, not bool(is_false[v]))] + [(dec[L], False) for L in range(2, int(level[v]) + 1)]
+        ng = P.nogood(r)
+        assert comp.contains(ng) or r in learned_ids, f"reason {r} of {v} is neither completion nor learned"
+        return lits(ng)
+
+    delta = lits(P.nogood(lc["conflict"]))
+    d, kappa, uip = oracle.first_uip(delta, pos, level, antecedent)
+    got = lits(P.nogood(lc["learned"]))
+    assert len(got) == lc["length"] == len(set(got))
+    assert got[0] == uip
+    assert set(got) == {l for l in d if level[l[0]] > 1}
+    assert lc["target"] == max(kappa, 1)
+    print(f"res k={k}: learned nogood of {len(got)} literals, target {lc['target']}")
     P.close()
