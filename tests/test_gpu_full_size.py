@@ -241,11 +241,13 @@ def _check_fwd_conflict(gpu, P, comp, k, asserting=False):
 
 
 # (conflict k, options): the benchmark's defaults, then the unit frontier
-# (the fastest propagation-round mode of the benchmark's comparison) and the
-# asserting-level backjump
+# (the fastest propagation-round mode of the benchmark's comparison, also on
+# 76 CTAs), the asserting-level backjump, and the Jeroslow-Wang and
+# decaying-activity decision scores
 FWD_CASES = [(1, {}), (3, {}), (8, {}), (25, {}),
-             (4, {"frontier": 2}), (15, {"frontier": 2}),
-             (6, {"backjump": 1})]
+             (4, {"frontier": 2}), (15, {"frontier": 2}), (7, {"frontier": 2, "grid_ctas": 76}),
+             (6, {"backjump": 1}),
+             (5, {"heuristic": 4}), (9, {"heuristic": 5})]
 
 
 @pytest.mark.parametrize("k,opts", FWD_CASES, ids=[f"k{k}-{'-'.join(f'{a}{b}' for a, b in o.items()) or 'default'}"
