@@ -349,6 +349,48 @@ int64_t asp_debug_nogood(asp_prog *p, uint32_t id, int32_t *lits, int64_t cap);
  * negative ASP_E_*. */
 int64_t asp_debug_learned(asp_prog *p, uint32_t *ids, int64_t cap);
 
+/* The completion nogoods (Section 2: the nogoods of each rule's body
+ * definition b_j <-> t_j & n_j, t_j <-> B+, n_j <-> not B-, head <- b_j, each
+ * atom's support nogood {Tp} u {Fb_j : head(j) = p}, one nogood per
+ * constraint) exactly as asp_load_ground builds them on the host, computed
+ * on the host alone (no device is touched, so it runs on machines without a
+ * GPU).  The program arguments are those of asp_load_ground; compact != 0
+ * takes the compact completion of asp_options.compact.  Variables are the
+ * library's: atoms 0..n_atoms-1, then b_j, t_j, n_j = n_atoms + 3j + 0/1/2
+ * for the headed rules j ordered by head atom (ties in input order).
+ *   n_vars, n_nogoods, n_literals  outputs (required)
+ *   off   host int64[n_nogoods + 1]: nogood i is lits[off[i] .. off[i+1])
+ *   lits  host int32[lits_cap]: literals (var << 1 | sign), sign 1 = F
+ * Pass off = lits = NULL to read the counts first.  Order: the nogoods of
+ * length 2..15 by length (an atom's rule nogoods and its own nogood
+ * together, atom by atom, then the constraints), then the longer ones, the
+ * unit nogoods, and one empty nogood per empty constraint.  Returns ASP_OK,
+ * ASP_E_ARG / ASP_E_RANGE as asp_load_ground does, or ASP_E_CAPACITY if
+ * lits_cap < n_literals.  Caller owns every buffer. */
+int asp_debug_completion(int32_t n_atoms, int32_t n_rules, const int32_t *head,
+                         const int64_t *pos_off, const int32_t *pos,
+                         const int64_t *neg_off, const int32_t *neg, int32_t compact,
+                         int64_t *n_vars, int64_t *n_nogoods, int64_t *n_literals,
+                         int64_t *off, int32_t *lits, int64_t lits_cap);
+
+/* The static decision scores of the headed rules (Section 4, Decision:
+ * occurrences and Jeroslow-Wang), as asp_load_ground computes them on the
+ * host, without a device.  For rule j of the library's order (headed rules
+ * by head atom, ties in input order): rule_index[j] = its input index,
+ * score_occ[j] = occurrences of its head atom in the completion's literals
+ * (heuristic ASP_HEUR_OCCURRENCE), score_jw[j] = sum of 2^(16 - |delta|)
+ * over the nogoods delta holding F b_j, plus the same over those holding
+ * F head(j) (heuristic ASP_HEUR_JW; nogoods longer than 16 add 0; saturates
+ * at 2^31 - 1).  n_headed (required) receives the number of headed rules;
+ * any of the three arrays may be NULL, the others hold cap entries.
+ * Returns ASP_OK, the errors of asp_load_ground's argument checks, or
+ * ASP_E_CAPACITY if cap < n_headed. */
+int asp_debug_rule_scores(int32_t n_atoms, int32_t n_rules, const int32_t *head,
+                          const int64_t *pos_off, const int32_t *pos,
+                          const int64_t *neg_off, const int32_t *neg, int32_t compact,
+                          int32_t *n_headed, int32_t *rule_index, uint32_t *score_occ,
+                          uint32_t *score_jw, int64_t cap);
+
 /* Test-only failure injection at the grid barrier of asp_solve (the
  * persistent kernel's phase barrier, Algorithm 1's steps run between them):
  * CTA stall_cta of the solver grid does not arrive at the first phase

@@ -62,7 +62,8 @@ EXPORTS = ["asp_default_options", "asp_load_ground", "asp_solve", "asp_solve_asy
            "asp_stats", "asp_free", "asp_last_error", "asp_debug_propagate", "asp_sweep",
            "asp_debug_state", "asp_debug_last_conflict", "asp_debug_nogood", "asp_debug_learned",
            "asp_build_info", "asp_debug_barrier", "asp_debug_fail_alloc", "asp_propagate_noalloc", "asp_trace", "asp_train_mlp",
-           "asp_mlp_score", "asp_batch_create", "asp_batch_run", "asp_batch_info", "asp_batch_free"]
+           "asp_mlp_score", "asp_batch_create", "asp_batch_run", "asp_batch_info", "asp_batch_free",
+           "asp_debug_completion", "asp_debug_rule_scores"]
 
 
 def library_path() -> str:
@@ -132,6 +133,10 @@ def lib(build_if_missing: bool = True):
         L.asp_train_mlp.restype = C.c_int
         L.asp_mlp_score.argtypes = [vp, vp, i64, vp]
         L.asp_mlp_score.restype = C.c_int
+        L.asp_debug_completion.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, i64]
+        L.asp_debug_completion.restype = C.c_int
+        L.asp_debug_rule_scores.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64]
+        L.asp_debug_rule_scores.restype = C.c_int
         _lib = L
         return L
 
@@ -335,6 +340,46 @@ class Program:
             buf = np.zeros(n, np.int32)
             lib().asp_debug_nogood(self.handle, int(nid), buf.ctypes.data, n)
         return buf[:n].copy()
+
+
+def _program_arrays(prog):
+    arrs = [np.ascontiguousarray(prog.head, np.int32), np.ascontiguousarray(prog.pos_off, np.int64),
+            np.ascontiguousarray(prog.pos, np.int32), np.ascontiguousarray(prog.neg_off, np.int64),
+            np.ascontiguousarray(prog.neg, np.int32)]
+    return arrs, [a.ctypes.data if a.size else None for a in arrs]
+
+
+def completion(prog, compact: bool = False):
+    """The library's completion nogoods, built on the host only
+    (asp_debug_completion): (n_vars, off int64[n + 1], lits int32) with
+    literals (var << 1 | sign), sign 1 = F, in the library's variables."""
+    L = lib()
+    keep, ptrs = _program_arrays(prog)
+    nv, nn, nl = C.c_int64(), C.c_int64(), C.c_int64()
+    args = [int(prog.n_atoms), int(prog.head.shape[0]), *ptrs, 1 if compact else 0,
+            C.byref(nv), C.byref(nn), C.byref(nl)]
+    _check(L.asp_debug_completion(*args, None, None, 0))
+    off = np.zeros(nn.value + 1, np.int64)
+    lits = np.zeros(max(nl.value, 1), np.int32)
+    _check(L.asp_debug_completion(*args, off.ctypes.data, lits.ctypes.data, int(lits.shape[0])))
+    return nv.value, off, lits[:nl.value]
+
+
+def rule_scores(prog, compact: bool = False):
+    """Library rule order and static decision scores, on the host only
+    (asp_debug_rule_scores): (rule_index, score_occ, score_jw), one entry per
+    headed rule in the library's order."""
+    L = lib()
+    keep, ptrs = _program_arrays(prog)
+    nh = C.c_int32()
+    args = [int(prog.n_atoms), int(prog.head.shape[0]), *ptrs, 1 if compact else 0, C.byref(nh)]
+    _check(L.asp_debug_rule_scores(*args, None, None, None, 0))
+    n = nh.value
+    idx = np.zeros(max(n, 1), np.int32)
+    occ = np.zeros(max(n, 1), np.uint32)
+    jw = np.zeros(max(n, 1), np.uint32)
+    _check(L.asp_debug_rule_scores(*args, idx.ctypes.data, occ.ctypes.data, jw.ctypes.data, int(idx.shape[0])))
+    return idx[:n], occ[:n], jw[:n]
 
 
 def build_info() -> dict:

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 SOURCES = [("solve.cu", [], "solve"), ("solve_units.cu", [], "solve_units"), ("batch.cu", [], "batch")]
 SOURCES += [("batch_kernel.cu", [f"-DBATCH_CONFIG={c}", f"-DBATCH_UNITS={u}"], f"batch_kernel_c{c}_u{u}")
             for c in (0, 1) for u in (0, 1)]
-SOURCES += [(f, [], f.split(".")[0]) for f in ("sweep.cu", "noalloc.cu", "mlp.cu", "api.cpp", "store.cpp")]
+SOURCES += [(f, [], f.split(".")[0]) for f in ("sweep.cu", "noalloc.cu", "mlp.cu", "api.cpp", "store.cpp",
+                                                  "host_completion.cpp")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
