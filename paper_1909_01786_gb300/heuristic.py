@@ -97,16 +97,22 @@ def fit(X: np.ndarray, y: np.ndarray, epochs: int = 60, learning_rate: float = 0
     sd[sd < 1e-6] = 1.0
     Z = ((X - mu) / sd).astype(np.float32)
     w = aspgpu.train_mlp(Z, y, init_weights(seed), epochs=epochs, learning_rate=learning_rate)
-    W1, b1, w2, b2 = split(w.copy())
-    # raw-feature network: W1' = W1 / sd, b1' = b1 - W1' mu; score = logit
-    W1r = W1 / sd[None, :]
-    b1r = b1 - W1r @ mu
-    out = np.concatenate([W1r.reshape(-1), b1r, w2, b2]).astype(np.float32)
+    out = fold_standardisation(w, mu, sd)
     p = 1.0 / (1.0 + np.exp(-forward_np(w, Z)))
     stats = dict(samples=int(X.shape[0]), positive=float(y.mean()) if y.size else 0.0,
                  train_logloss=float(-np.mean(y * np.log(p + 1e-7) + (1 - y) * np.log(1 - p + 1e-7))),
                  train_accuracy=float(np.mean((p > 0.5) == (y > 0.5))))
     return out, stats
+
+
+def fold_standardisation(w: np.ndarray, mu: np.ndarray, sd: np.ndarray) -> np.ndarray:
+    """Weights of a network trained on standardised features (x - mu) / sd,
+    rewritten for raw features: W1' = W1 / sd, b1' = b1 - W1' mu (the same
+    logit for every x)."""
+    W1, b1, w2, b2 = split(np.asarray(w, np.float32).copy())
+    W1r = W1 / sd[None, :]
+    b1r = b1 - W1r @ mu
+    return np.concatenate([W1r.reshape(-1), b1r, w2, b2]).astype(np.float32)
 
 
 def forward_np(w: np.ndarray, X: np.ndarray) -> np.ndarray:
