@@ -66,3 +66,63 @@ def test_batch_blocks_equal_the_whole_batch():
     whole = batch_programs(6, rules_per_atom=2, lo=50, hi=300, config_id=12)
     part = batch_programs(3, rules_per_atom=2, lo=50, hi=300, config_id=12, first_index=3)
     assert all(_same(x, y) for x, y in zip(whole[3:], part))
+
+
+# ------------------------------------------------ workload families
+
+def _proper_colourings(n, edges):
+    """Every map V -> {0,1,2} with no edge inside one colour, by enumeration."""
+    out = set()
+    for code in range(3 ** n):
+        col = [(code // 3 ** v) % 3 for v in range(n)]
+        if all(col[u] != col[v] for (u, v) in edges):
+            out.add(tuple(col))
+    return out
+
+
+def test_colouring_program_answer_sets_are_the_proper_colourings():
+    """The 3-colouring encoding's answer sets (oracle CDNL, itself pinned
+    against brute force) decode one to one to the proper colourings of the
+    graph, enumerated directly."""
+    import oracle
+    from synth.programs import coloring_atom, coloring_program
+    for edges in ([(0, 1), (1, 2), (2, 0)], [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2)],
+                  [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)], [(0, 1), (2, 3), (3, 4)]):
+        n = 1 + max(max(e) for e in edges)
+        prog = coloring_program(n, edges=np.array(edges))
+        status, models, _ = oracle.cdnl(prog)
+        want = _proper_colourings(n, edges)
+        got = set()
+        for m in models:
+            col = []
+            for v in range(n):
+                cs = [c for c in range(3) if m[coloring_atom(n, v, c)]]
+                assert len(cs) == 1
+                for c in range(3):            # ncol(v,c) holds exactly when col(v,c) does not
+                    assert m[coloring_atom(n, v, c, True)] == (c not in cs)
+                col.append(cs[0])
+            got.add(tuple(col))
+        assert len(models) == len(got) == len(want) and got == want
+        assert status == (oracle.SAT if want else oracle.UNSAT)
+
+
+def test_colouring_program_shape_and_degree():
+    from synth.programs import coloring_graph, coloring_program
+    edges = coloring_graph(2000, 4.5, seed_index=0)
+    assert (edges[:, 0] < edges[:, 1]).all() and np.unique(edges, axis=0).shape[0] == edges.shape[0]
+    assert abs(2 * edges.shape[0] / 2000 - 4.5) < 0.3          # average degree of G(n, 4.5 / (n - 1))
+    prog = coloring_program(50, 4.5, seed_index=0)
+    e = coloring_graph(50, 4.5, seed_index=0).shape[0]
+    assert prog.n_atoms == 300
+    assert prog.head.shape[0] == 6 * 50 + 4 * 50 + 3 * e
+    assert int((prog.head >= 0).sum()) == 300
+
+
+def test_batch_sizes_are_log_uniform():
+    from synth.programs import batch_sizes
+    _, n = batch_sizes(4096)
+    assert n.min() >= 200 and n.max() <= 20000
+    u = (np.log(n) - np.log(200)) / (np.log(20000) - np.log(200))
+    # each quarter of the log range holds about a quarter of the programs
+    counts = np.histogram(u, bins=4, range=(0, 1))[0]
+    assert (np.abs(counts - 1024) < 120).all(), counts
