@@ -152,3 +152,45 @@ def test_argument_errors_and_capacity():
     one = np.zeros(1, np.int32)
     assert L.asp_debug_rule_scores(prog.n_atoms, n_rules, *ptrs, 0, C.byref(nh), one.ctypes.data, None, None,
                                    1) == -5
+
+
+def _raw(n_atoms, head, pos_off, pos, neg_off, neg):
+    """asp_debug_completion on raw arrays (count-only call)."""
+    L = aspgpu.lib()
+    arrs = [np.ascontiguousarray(head, np.int32), np.ascontiguousarray(pos_off, np.int64),
+            np.ascontiguousarray(pos, np.int32), np.ascontiguousarray(neg_off, np.int64),
+            np.ascontiguousarray(neg, np.int32)]
+    nv, nn, nl = C.c_int64(), C.c_int64(), C.c_int64()
+    rc = L.asp_debug_completion(int(n_atoms), int(arrs[0].shape[0]), *[a.ctypes.data if a.size else None for a in arrs],
+                                0, C.byref(nv), C.byref(nn), C.byref(nl), None, None, 0)
+    return rc, L.asp_last_error().decode()
+
+
+def test_program_validator_rejects_malformed_arrays():
+    """The argument checks asp_load_ground runs before any device work
+    (invalid or truncated program arrays give ASP_E_ARG / ASP_E_RANGE with a
+    message, never a crash)."""
+    ok = _raw(3, [0, -1], [0, 1, 2], [1, 2], [0, 0, 1], [0])
+    assert ok[0] == 0
+    cases = [
+        ((3, [0, 5], [0, 1, 2], [1, 2], [0, 0, 1], [0]), -2, "head"),               # head out of range
+        ((3, [0, -2], [0, 1, 2], [1, 2], [0, 0, 1], [0]), -2, "head"),              # head below -1
+        ((3, [0, -1], [0, 1, 2], [1, 7], [0, 0, 1], [0]), -2, "body"),              # body atom out of range
+        ((3, [0, -1], [0, 1, 2], [1, 2], [0, 0, 1], [-1]), -2, "body"),             # negative body atom
+        ((3, [0, -1], [1, 1, 2], [1, 2], [0, 0, 1], [0]), -1, "start at 0"),        # offsets not from 0
+        ((3, [0, -1], [0, 2, 1], [1, 2], [0, 0, 1], [0]), -1, "monotone"),          # offsets decreasing
+        ((-1, [0, -1], [0, 1, 2], [1, 2], [0, 0, 1], [0]), -1, "negative"),         # negative atom count
+    ]
+    for args, code, word in cases:
+        rc, msg = _raw(*args)
+        assert rc == code, (args, rc, msg)
+        assert word in msg, (word, msg)
+    # a positive body referenced by offsets but not given
+    L = aspgpu.lib()
+    head = np.array([0], np.int32)
+    off1 = np.array([0, 1], np.int64)
+    off0 = np.array([0, 0], np.int64)
+    nv, nn, nl = C.c_int64(), C.c_int64(), C.c_int64()
+    rc = L.asp_debug_completion(2, 1, head.ctypes.data, off1.ctypes.data, None, off0.ctypes.data, None, 0,
+                                C.byref(nv), C.byref(nn), C.byref(nl), None, None, 0)
+    assert rc == -1 and "null" in L.asp_last_error().decode()

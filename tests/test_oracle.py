@@ -283,7 +283,9 @@ def test_c8_needs_stability_check():
 
 
 def test_crosscheck_script_on_a_slice():
-    """The committed O2-vs-O1 cross-check (run on 10^4 programs offline)
-    passes on a slice of the same family."""
+    """The committed O2-vs-O1 cross-check (run on 4 x 10^4 programs of the
+    tiny family and 10^4 denser ones offline) passes on a slice of each."""
     from oracle import crosscheck
     assert crosscheck.main(["--count", "12", "--first", "9000", "--workers", "2"]) == 0
+    assert crosscheck.main(["--count", "8", "--first", "9000", "--workers", "2", "--rules", "60",
+                            "--constraints", "4"]) == 0
