@@ -70,3 +70,30 @@ def test_bad_arguments_are_rejected_before_any_device_work():
     assert rc in (-2, -7)                    # RANGE, or no device checked first
     rc = L.asp_load_ground(2, 1, head.ctypes.data, off.ctypes.data, None, off.ctypes.data, None, None, None)
     assert rc == -1
+
+
+def _declared_arity():
+    """Parameter count of every asp_* function declared in the header."""
+    text = open(os.path.join(ROOT, "include", "aspgpu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(asp_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text):
+        params = m.group(2).strip()
+        if params in ("", "void"):
+            out[m.group(1)] = 0
+            continue
+        depth, n = 0, 1
+        for ch in params:
+            depth += ch == "("
+            depth -= ch == ")"
+            n += ch == "," and depth == 0
+        out[m.group(1)] = n
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    L = aspgpu.lib()
+    arity = _declared_arity()
+    assert set(arity) == set(aspgpu.EXPORTS)
+    for name, n in arity.items():
+        assert len(getattr(L, name).argtypes) == n, (name, n)
